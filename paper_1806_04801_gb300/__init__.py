@@ -1,0 +1,7 @@
+"""GB300-native harmonic surface mapping algorithm (HSMA, arXiv:1806.04801).
+
+The compute path is the CUDA library ``libhsma.so`` (sources in ``csrc/``),
+reached through the C ABI declared in ``include/hsma.h``; ``hsma`` is the thin
+ctypes binding.  ``inputs`` holds the seeded synthetic workloads.
+"""
+__all__ = ["hsma", "inputs"]

@@ -1,0 +1,322 @@
+"""Benchmark of the HSMA hot path on GB300.
+
+A step is one full update step (in-set, near-field sums at particles and
+monitoring points, fit, surface images and their sums, energy and forces) of
+one periodic system of 100000 charges (p = 12, 2000 monitoring points,
+Q = 8000 -> F2 = 1597, Rs = 1.5 L), FP32 pair sums with double-float
+accumulation, FP64 fit and energy.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (a 256 MB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own system (weak scaling; no collective on
+the data path).  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("systems/sec and pair-interactions/s vs FP32 roofline at rel. energy err ≤1e-6; p50/p99")
+FP32_LANES_PER_SM = 128          # FP32 lanes per SM (GB300)
+OPS_POT_FIELD = 13               # FP32 lane instructions per potential+field pair (minimal form)
+OPS_POT = 7                      # FP32 lane instructions per potential-only pair
+RECIPE_SMS = 152
+RECIPE_MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_tc"])
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.path = None
+        self.proc = None
+
+    def start(self, gpu_index: int):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(xyz, q, w, budget_s: float = 12.0, threads: int | None = None):
+    """Time the oracle (as it stands) on a bounded sample of the workload and
+    scale to systems/s: the monitoring-point sums and the fit are run in full,
+    the particle sums on a sample whose cost is extrapolated linearly in N."""
+    from oracle import hsma as oh
+    threads = threads or os.cpu_count() or 1
+    F2, _ = oh.fib_from_points(w.Q)
+    plan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    n = len(q)
+    t0 = time.perf_counter()
+    oh.energy_forces(xyz, q, plan, nthreads=threads, sample=np.arange(0, n, max(1, n // 16))[:16])
+    t_fixed = time.perf_counter() - t0
+    # particle sums: size a sample to fill the remaining budget
+    per_particle = None
+    k = 64
+    from oracle import coulomb, inset
+    c = oh.centre_positions(xyz, w.box, w.bc)
+    s_xyz, s_q, _, _ = inset(c, q, np.asarray(w.box, dtype=np.float64), w.bc, w.R)
+    while True:
+        idx = np.linspace(0, n - 1, k).astype(np.int64)
+        t0 = time.perf_counter()
+        coulomb(s_xyz, s_q, c[idx], tskip=idx, field=True, nthreads=threads)
+        dt = time.perf_counter() - t0
+        per_particle = dt / k
+        if dt > 1.0 or k >= n:
+            break
+        k = min(n, int(k * max(2.0, 1.5 / max(dt, 1e-3))))
+    t_system = t_fixed + per_particle * n
+    return {"systems_per_s": 1.0 / t_system, "threads": threads, "t_fixed_s": t_fixed,
+            "particles_sampled": int(k), "n_inset": int(s_xyz.shape[0]),
+            "pairs_per_s": (n * (s_xyz.shape[0] - 1)) / (per_particle * n)}
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the FP64 CPU oracle on the host cores, on a bounded
+    sample of the same workload, for each of W + K steps."""
+    if rank != 0:
+        return 0
+    from paper_1806_04801_gb300 import inputs as I
+    w = I.LARGE_PERIODIC
+    xyz, q = I.large_periodic(args.n)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(xyz, q, w, budget_s=4.0)
+        if i >= args.warmup:
+            vals.append(r["systems_per_s"])
+    v = statistics.median(vals)
+    sample = (f"per step: full monitoring-point sums + fit + 16 particles, then particle near-field sums on "
+              f"{r['particles_sampled']} of {args.n} particles extrapolated linearly in N")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "systems/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "N": args.n, "p": w.p, "Kmon": w.Kmon, "Q": w.Q, "Rs": w.R},
+            "cpu_baseline": {"value": v, "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_1806_04801_gb300 import build as B
+    B.build()
+    from paper_1806_04801_gb300 import hsma
+    from paper_1806_04801_gb300 import inputs as I
+
+    w = I.LARGE_PERIODIC
+    xyz, q = I.uniform_gauss(args.n, w.box, seed_offset=1 + 1000 * rank) if rank else I.large_periodic(args.n)
+    dev = torch.device("cuda", local)
+    dx = torch.as_tensor(xyz).to(dev)
+    dq = torch.as_tensor(q).to(dev)
+    plan = hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=args.precision, profile=True)
+    info = plan.info()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.energy_forces(dx, dq)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler()
+    if rank == 0:
+        clocks.start(local)
+        time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, pair_ms, launches0 = [], [], hsma.kernel_launches()
+    n_inset = None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U, F, _, n_inset = plan.energy_forces(dx, dq)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pair_ms.append(plan.last_timings()[1])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = hsma.kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    systems_per_s = world * args.steps / (total_ms / 1000.0)
+    n = args.n
+    nmon = info["n_mon_targets"]
+    pairs_pf = n * (n_inset - 1)
+    pairs_p = nmon * n_inset
+    pairs_surf = n * 2 * (info["F2"] - 1)
+    pairs_total = pairs_pf + pairs_p + pairs_surf
+    pair_avg_ms = sum(pair_ms) / len(pair_ms)
+    ops = OPS_POT_FIELD * pairs_pf + OPS_POT * pairs_p
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peak_ops = sms * FP32_LANES_PER_SM * RECIPE_MAX_SM_MHZ * 1e6
+    achieved = ops / (pair_avg_ms / 1000.0)
+
+    # end to end through the public API with host buffers (pinned)
+    hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    hq = torch.empty((n,), dtype=torch.float64, pin_memory=True)
+    hx.copy_(torch.as_tensor(xyz))
+    hq.copy_(torch.as_tensor(q))
+    hxn, hqn = hx.numpy(), hq.numpy()
+    plan.energy_forces(hxn, hqn)
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.energy_forces(hxn, hqn)
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+    e2e_step = statistics.median(e2e_ms)
+
+    accuracy = None
+    if not args.no_check and rank == 0:
+        with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as p64:
+            U64, F64, _, _ = p64.energy_forces(dx, dq)
+        Uc, Fc, _, _ = plan.energy_forces(dx, dq)
+        dF = (Fc - F64).double()
+        accuracy = {"reference": "FP64 GPU path (same inputs)",
+                    "rel_energy_err": abs(Uc - U64) / abs(U64),
+                    "rms_force_err_rel": float(dF.pow(2).mean().sqrt() / F64.pow(2).mean().sqrt()),
+                    "energy": Uc, "energy_fp64": U64}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        r = cpu_oracle_rate(xyz, q, w)
+        cpu = {"value": r["systems_per_s"], "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
+               "sample": (f"full monitoring-point sums and fit, near-field particle sums on "
+                          f"{r['particles_sampled']} of {n} particles, extrapolated linearly in N"),
+               "pairs_per_s": r["pairs_per_s"]}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    step_sorted = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": systems_per_s, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+        "pair_interactions_per_s": world * pairs_total * args.steps / (total_ms / 1000.0),
+        "latency_ms": {"p50": float(np.percentile(step_sorted, 50)), "p99": float(np.percentile(step_sorted, 99))},
+        "config": {"workload": w.name, "N": n, "p": w.p, "Kmon": w.Kmon, "Q": w.Q, "F2": info["F2"],
+                   "N_o": info["n_images"], "Rs": w.R, "N_s": int(n_inset), "precision": args.precision,
+                   "pairs_per_step": {"pot_field": pairs_pf, "pot_only_monitor": pairs_p, "surface": pairs_surf},
+                   "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "kernel": "pair_fp32_kernel" if args.precision != "fp64" else "pair_fp64_kernel",
+                     "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "T FP32 lane-instructions/s", "frac": achieved / peak_ops, "traffic": None,
+                     "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
+                                   f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",
+                     "kernel_ms": pair_avg_ms, "share_of_step": pair_avg_ms / ms_per_step},
+        "e2e": {"value": 1000.0 / e2e_step, "unit": "systems/s", "ms_per_step": e2e_step,
+                "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 24 + 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "phases_ms": dict(zip(["inset", "near_field", "chunk_reduce", "fit", "surface_charges", "surface_pairs",
+                               "finalize", "total"], plan.last_timings())),
+        "accuracy": accuracy,
+        "cpu_baseline": cpu,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,230 @@
+/*
+ * hsma.h -- C ABI of the GB300-native harmonic surface mapping algorithm
+ * (HSMA; Zhao, Liang & Xu, "Harmonic surface mapping algorithm for fast
+ * electrostatic sums", arXiv:1806.04801).
+ *
+ * The library computes the electrostatic energy and forces of N point charges
+ * in a box whose boundary condition is represented by infinitely many image
+ * charges (Sec. II, Eq. "sum"): periodic copies, or the sign-alternating
+ * reflections of a grounded (perfectly conducting) box (Eq. "diel" at
+ * gamma = -1).  The method (Sec. II.A-C):
+ *   (a) sums the N sources and their images inside an auxiliary sphere of
+ *       radius Rs directly (Phi_in) at the particles and at monitoring points;
+ *   (b) evaluates the harmonic basis r^n Y_n^m (Eq. "harmonic");
+ *   (c) fits the coefficients A_nm of the far-image potential Phi_out by least
+ *       squares to the boundary condition at the monitoring points;
+ *   (d) maps Phi_out onto point charges and dipole pairs on the sphere by
+ *       Green's second identity and Fibonacci integration (Eqs. "green",
+ *       "cd", "integrals"), and sums their potential and field at the
+ *       particles.
+ * Every step runs in CUDA kernels on the device.
+ *
+ * Conventions.  Gaussian units: potential q/r, energy
+ * U = 1/2 sum_i q_i phi'(r_i) where phi' omits only the particle's own
+ * singular term, force F_i = q_i E'(r_i).  Positions are given in the box
+ * frame [0, L_x) x [0, L_y) x [0, L_z), row-major n x 3, FP64.  Periodic
+ * inputs are wrapped into the box; grounded inputs must lie strictly inside.
+ *
+ * Errors.  Every function returns HSMA_OK (0) or a negative code; no
+ * exception crosses the ABI.  hsma_strerror() names a code.  After an error
+ * the output buffers are unspecified; the plan stays usable unless the code
+ * is HSMA_E_CUDA.
+ *
+ * Ownership.  The caller owns particles and output buffers.  A plan owns its
+ * device-resident matrices and its workspace; it is not thread-safe (use one
+ * plan per host thread, or the serving API).  All device work of a plan runs
+ * on the stream given in hsma_opts (NULL = the legacy default stream).
+ */
+#ifndef HSMA_H
+#define HSMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define HSMA_OK 0
+#define HSMA_E_ARG (-1)          /* invalid argument (size, NULL, range)            */
+#define HSMA_E_NONNEUTRAL (-2)   /* periodic system with |sum q| > 1e-12 sum |q|     */
+#define HSMA_E_OUT_OF_BOX (-3)   /* grounded box: particle on/outside a wall, or NaN */
+#define HSMA_E_COINCIDENT (-4)   /* two charges at one point: non-finite result      */
+#define HSMA_E_OOM (-5)          /* device or pinned host allocation failed          */
+#define HSMA_E_TIMEOUT (-6)      /* a bounded device-side wait ran out               */
+#define HSMA_E_CUDA (-7)         /* CUDA runtime error (context may be unusable)     */
+#define HSMA_E_ILLCOND (-8)      /* fitting matrix numerically rank deficient        */
+#define HSMA_E_NOT_FOUND (-9)    /* unknown ticket / item                            */
+#define HSMA_E_AGAIN (-10)       /* serving: result not ready yet                    */
+#define HSMA_E_CAPACITY (-11)    /* serving: request larger than the memory budget   */
+
+/* ------------------------------------------------------------ parameters */
+typedef struct hsma_plan_s *hsma_plan_t;
+
+typedef enum { HSMA_BC_PERIODIC = 0, HSMA_BC_GROUNDED = 1 } hsma_bc;
+
+/* Arithmetic of the update step.
+ *  HSMA_FP64          everything in FP64 (parity form).
+ *  HSMA_FP32_ACC64    pair sums with FP32 differences (positions split into
+ *                     two FP32 words), FP32 rsqrt and FP32 partial sums folded
+ *                     into double-float accumulators; fit, mapping and energy
+ *                     in FP64.
+ *  HSMA_FP32_TC_FIT   as HSMA_FP32_ACC64, but the fit A = M+ b runs on the
+ *                     tensor cores as a split-BF16 product with FP32
+ *                     accumulation plus one refinement step. */
+typedef enum { HSMA_FP64 = 0, HSMA_FP32_ACC64 = 1, HSMA_FP32_TC_FIT = 2 } hsma_precision;
+
+typedef struct {
+    int precision;      /* hsma_precision                         (default 1) */
+    double dr_rel;      /* Delta r / Rs of Eq. "cd"; <= 0: 1e-5 periodic,
+                           1e-4 grounded (Sec. III)                         */
+    int fib_F2;         /* > 0: Fibonacci number F2 of the surface quadrature;
+                           0: chosen from Q as the F2 whose 6(F2+1) is nearest
+                           to Q (ties to the larger)                         */
+    int reserved0;      /* must be 0                                         */
+    void *stream;       /* cudaStream_t for all device work; NULL = default  */
+    int use_graphs;     /* 1 = capture the update step in a CUDA graph (default) */
+    int profile;        /* 1 = record per-phase CUDA-event timings           */
+} hsma_opts;
+
+/* Fill *opts with the defaults above.  Returns HSMA_OK or HSMA_E_ARG. */
+int hsma_opts_default(hsma_opts *opts);
+
+/* ------------------------------------------------------------------ plan */
+/* Preparation step (Sec. II.C; Table I, upper half): monitoring points
+ * (Fibonacci grid on the circumsphere of the box for periodic boxes, Sec.
+ * II.A; a near-uniform lattice on the walls otherwise), the fitting matrix
+ * M of basis values at the monitoring points (periodic: B(x_i) - B(x~_i),
+ * with the constant column dropped), its pseudo-inverse by FP64 Householder
+ * QR, and the basis at the 2(F2+1) Fibonacci integration directions on the
+ * sphere Rs (Sec. II.B).  All of it stays resident on the device.
+ *
+ *   box   [L_x, L_y, L_z] > 0 (host pointer)
+ *   bc    hsma_bc
+ *   p     harmonic order P, 1 <= p <= 40; N_b = (p+1)^2 basis functions
+ *   R     auxiliary sphere radius Rs; must exceed the circumradius of the box
+ *   Q     requested number of surface points (used when opts->fib_F2 == 0)
+ *   Kmon  number of monitoring points, Kmon >= N_b, Kmon <= 16384
+ *   opts  NULL for defaults
+ * On success *out receives a new plan (destroy with hsma_plan_destroy).
+ * Errors: HSMA_E_ARG, HSMA_E_OOM, HSMA_E_ILLCOND, HSMA_E_CUDA. */
+int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, int Q, int Kmon,
+              const hsma_opts *opts);
+
+void hsma_plan_destroy(hsma_plan_t plan);
+
+typedef struct {
+    int bc, p, n_basis, n_cols;  /* n_cols: fitted columns (N_b - 1 periodic)       */
+    int Kmon, n_mon_targets;     /* monitoring points; targets (2 Kmon periodic)    */
+    int F2, F1, n_images;        /* quadrature; N_o = 6(F2+1) images                */
+    int n_shifts;                /* image shifts k tested when building the in-set  */
+    double Rs, R0, alpha, dr;    /* sphere, circumradius, Rs/R0, Delta r            */
+    double cond_estimate;        /* max|R_jj| / min|R_jj| of the QR factor          */
+    int precision;
+} hsma_plan_info_t;
+
+int hsma_plan_get_info(hsma_plan_t plan, hsma_plan_info_t *info);
+
+/* Change the stream a plan works on (NULL = legacy default stream). */
+int hsma_plan_set_stream(hsma_plan_t plan, void *stream);
+
+/* Change the arithmetic of later update steps (hsma_precision). */
+int hsma_plan_set_precision(hsma_plan_t plan, int precision);
+
+/* Device bytes the plan's workspace needs for a system of n particles
+ * (for admission control).  *bytes is an upper bound. */
+int hsma_plan_footprint(hsma_plan_t plan, int64_t n, size_t *bytes);
+
+/* Copy a plan matrix to host memory (FP64, row-major), for inspection and
+ * tests.  which: 0 = monitoring points (n_mon_targets x 3, periodic: the
+ * Kmon points x_i followed by their partners x~_i), 1 = fitting matrix M
+ * (Kmon x n_cols), 2 = pseudo-inverse M+ (n_cols x Kmon), 3 = integration
+ * directions (2(F2+1) x 3 unit vectors), 4 = integration weights
+ * (2(F2+1)), 5 = basis at the integration points (2(F2+1) x N_b).
+ * count is the capacity of host_out in doubles. */
+int hsma_plan_get_matrix(hsma_plan_t plan, int which, double *host_out, int64_t count);
+
+/* ---------------------------------------------------------------- update */
+typedef struct {
+    int64_t n;          /* number of particles N >= 1                     */
+    const double *xyz;  /* n x 3, box frame (see top)                     */
+    const double *q;    /* n charges                                      */
+    int on_device;      /* 1: xyz, q and the output arrays are device
+                           pointers; 0: host pointers (copied in and out) */
+} hsma_particles;
+
+typedef struct {
+    double energy;      /* U (Gaussian units)                                */
+    double *forces;     /* n x 3 caller-owned, or NULL                       */
+    double *potentials; /* n caller-owned, or NULL: phi'(r_i)                */
+    int64_t n_inset;    /* N_s: sources and images inside the sphere          */
+    int n_images;       /* N_o surface images                                */
+} hsma_out;
+
+/* Update step (Sec. II.C; Table I, lower half) for one configuration:
+ * in-set generation, the near-field sums Phi_in and E_in at the particles
+ * and at the monitoring points (Sec. II.A), the right-hand side and the fit
+ * A = M+ b, the surface images Q_j (Sec. II.B) and their potential and field
+ * at the particles, energy and forces.  Returns after the energy is on the
+ * host; forces/potentials are complete on return.
+ * Errors: HSMA_E_ARG, HSMA_E_NONNEUTRAL, HSMA_E_OUT_OF_BOX,
+ * HSMA_E_COINCIDENT, HSMA_E_OOM, HSMA_E_TIMEOUT, HSMA_E_CUDA. */
+int hsma_energy_forces(hsma_plan_t plan, const hsma_particles *x_q, hsma_out *out);
+
+/* Many independent systems that share one plan, in one persistent pass of
+ * device work.  System s holds particles offsets[s] .. offsets[s+1]-1 of the
+ * concatenated arrays in *all (offsets: host array of nsys+1 increasing
+ * values, offsets[0] = 0).  energies: host array of nsys.  forces /
+ * potentials: concatenated (offsets[nsys] x 3 / offsets[nsys]) in the same
+ * memory space as *all, or NULL.  An error in one system fails the call;
+ * status (host array of nsys, or NULL) receives each system's code. */
+int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offsets,
+                               const hsma_particles *all, double *energies, double *forces,
+                               double *potentials, int *status);
+
+/* ------------------------------------------------------- direct sums */
+/* Coulomb sums of Sec. II.A (Phi_in) on their own:
+ *   pot[t]   = sum_s q_s / |x_t - y_s|
+ *   field[t] = sum_s q_s (x_t - y_s) / |x_t - y_s|^3
+ * over ns sources (src: ns x 4 doubles x, y, z, q) and nt targets (tgt:
+ * nt x 3), all device pointers.  A pair at distance exactly 0 is skipped.
+ * field may be NULL.  precision as in hsma_precision (0 or 1).
+ * stream: cudaStream_t or NULL.  Errors: HSMA_E_ARG, HSMA_E_OOM,
+ * HSMA_E_CUDA. */
+int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tgt, double *pot,
+                     double *field, int precision, void *stream);
+
+/* Harmonic basis of Eq. "harmonic" at np points (device pointers; pts
+ * np x 3, out np x (p+1)^2 row-major): the orthonormal real solid harmonics
+ * (|x|/Rs)^n Y_nm, index k = n^2 + n + m, m > 0 the cosine and m < 0 the sine
+ * part, without the Condon-Shortley phase.  Errors: HSMA_E_ARG, HSMA_E_CUDA. */
+int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, void *stream);
+
+/* --------------------------------------------------------- inspection */
+const char *hsma_strerror(int code);
+const char *hsma_version(void);
+
+/* Number of kernel launches this library has issued (all plans, all
+ * threads) since it was loaded; graph replays count each kernel node. */
+int64_t hsma_kernel_launches(void);
+
+/* Per-phase device times (milliseconds) of the plan's last update step,
+ * when opts.profile was set: [0] in-set, [1] near-field pair sums,
+ * [2] chunk reduction, [3] fit, [4] surface images, [5] surface pair sums,
+ * [6] energy/forces, [7] total.  n: capacity of ms.  Returns the number of
+ * entries written, or a negative code. */
+int hsma_last_timings(hsma_plan_t plan, double *ms, int n);
+
+/* Intermediates of the plan's last single-system update, copied to host
+ * (FP64): which 0 = coefficients A (N_b, A_00 = 0 periodic), 1 = right-hand
+ * side b (Kmon), 2 = Phi_in at the monitoring targets (n_mon_targets),
+ * 3 = Phi_in at the particles (n), 4 = Phi_out at the particles (n).
+ * Returns the number of values written or a negative code. */
+int64_t hsma_last_get(hsma_plan_t plan, int which, double *host_out, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSMA_H */

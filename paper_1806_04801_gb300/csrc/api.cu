@@ -1,0 +1,1013 @@
+// C ABI of libhsma (declared in include/hsma.h): plan construction
+// (preparation step, Sec. II.C) and the update step orchestration.  All
+// arithmetic of the method runs in the kernels of the other translation
+// units; this file validates arguments, lays out device memory and enqueues
+// work on the plan's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hsma {
+
+std::atomic<long long> g_launches{0};
+static thread_local char g_cuda_err[384];
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
+             cudaGetErrorString(e));
+}
+
+int surface_targets_per_block();
+
+}  // namespace hsma
+
+using namespace hsma;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kInsetBlock = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over one device allocation.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *b) : base((char *)b) {}
+    template <class T>
+    T *take(size_t count)
+    {
+        off = align_up(off, 256);
+        T *p = base ? (T *)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+struct Workspace {
+    double *xyz = nullptr, *q = nullptr;            // staged inputs (host-input calls)
+    double *forces = nullptr, *pot = nullptr;       // staged outputs (host-output calls)
+    float4 *src_hi = nullptr, *src_lo = nullptr;    // in-set, FP32 split form
+    double4_32a *src64 = nullptr;                       // in-set, FP64
+    int *counts = nullptr;
+    long long *ns = nullptr;
+    float4 *partials = nullptr;
+    double *phi_tgt = nullptr, *e_part = nullptr;
+    double *b = nullptr, *A = nullptr;
+    double2 *img = nullptr;
+    double *phi_out = nullptr, *e_out = nullptr;
+    double *energy = nullptr;
+    int *status = nullptr;
+    int *ctrl = nullptr;                            // work counters
+    SysDesc *sys = nullptr;
+    float *tc_work = nullptr;
+};
+
+struct BatchShape {
+    int nsys = 0;
+    long long n_total = 0, cap_total = 0, cnt_total = 0, rec_total = 0, tgt_total = 0;
+    int items = 0, surf_items = 0, nblk_max = 1;
+    long long max_tgt = 0;
+    std::vector<SysDesc> sys;
+};
+
+}  // namespace
+
+struct hsma_plan_s {
+    double L[3];
+    int bc, P, Nb, ncols, K, nmon, F2, F1, ndir, nshifts;
+    double Rs, R0, dr, alpha, cond;
+    int precision, use_graphs, profile, mon_faces;
+    cudaStream_t stream;
+    int num_sms, ctas[3];
+    // plan-resident device data
+    void *plan_mem = nullptr;
+    double4_32a *mon64 = nullptr;
+    float4 *mon_hi = nullptr, *mon_lo = nullptr;
+    double *Mrow = nullptr, *Mp = nullptr, *Bq = nullptr, *norm = nullptr;
+    double4_32a *dirs = nullptr;
+    int4 *shifts = nullptr;
+    void *tc_hi = nullptr, *tc_lo = nullptr;
+    // workspace
+    void *ws_mem = nullptr;
+    size_t ws_cap = 0;
+    Workspace ws;
+    // pinned host staging
+    void *hpin = nullptr;
+    size_t hpin_cap = 0;
+    // last call
+    int last_nsys = 0;
+    long long last_n = 0;
+    BatchShape last_shape;
+    cudaEvent_t ev[8] = {};
+    bool events_ready = false;
+    double last_ms[8] = {};
+    bool have_timings = false;
+};
+
+namespace {
+
+std::vector<long long> fibonacci_list()
+{
+    std::vector<long long> f = {1, 2};
+    while (f.back() < 100000000LL) f.push_back(f[f.size() - 1] + f[f.size() - 2]);
+    return f;
+}
+
+// F2 such that 6(F2+1) is nearest to Q (ties to the larger F2); F1 its predecessor.
+void fib_from_q(int Q, int *F2, int *F1)
+{
+    auto f = fibonacci_list();
+    long long bestd = -1;
+    for (size_t i = 1; i < f.size(); ++i) {
+        long long d = llabs(6 * (f[i] + 1) - Q);
+        if (bestd < 0 || d < bestd || (d == bestd && f[i] > *F2)) {
+            bestd = d;
+            *F2 = (int)f[i];
+            *F1 = (int)f[i - 1];
+        }
+    }
+}
+
+bool fib_pred(int F2, int *F1)
+{
+    auto f = fibonacci_list();
+    for (size_t i = 1; i < f.size(); ++i)
+        if (f[i] == F2) {
+            *F1 = (int)f[i - 1];
+            return true;
+        }
+    return false;
+}
+
+int shells(double Rs, double La)
+{
+    int k = 0;
+    while ((k + 1) * La - 0.5 * La < Rs) ++k;
+    return k;
+}
+
+int map_status(int st)
+{
+    if (st & ST_OUT_OF_BOX) return HSMA_E_OUT_OF_BOX;
+    if (st & ST_NONNEUTRAL) return HSMA_E_NONNEUTRAL;
+    if (st & ST_TIMEOUT) return HSMA_E_TIMEOUT;
+    if (st & ST_CAPACITY) return HSMA_E_ARG;
+    if (st & ST_COINCIDENT) return HSMA_E_COINCIDENT;
+    return HSMA_OK;
+}
+
+int ensure_pinned(hsma_plan_s *p, size_t bytes)
+{
+    if (bytes <= p->hpin_cap) return HSMA_OK;
+    if (p->hpin) cudaFreeHost(p->hpin);
+    p->hpin = nullptr;
+    p->hpin_cap = 0;
+    size_t nb = std::max(bytes, (size_t)65536);
+    HSMA_CUDA_TRY(cudaMallocHost(&p->hpin, nb));
+    p->hpin_cap = nb;
+    return HSMA_OK;
+}
+
+// Work decomposition of a batch: targets per block, source chunks per system,
+// work items, surface blocks.  Pure host arithmetic.
+void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precision, BatchShape *sh)
+{
+    sh->nsys = nsys;
+    sh->sys.assign(nsys, SysDesc{});
+    const int TB = pair_targets_per_block(precision);
+    const int STB = surface_targets_per_block();
+    const int tile = (precision == HSMA_FP64) ? 256 : 512;
+    const double vsphere = 4.0 / 3.0 * kPi * p->Rs * p->Rs * p->Rs;
+    const double vbox = p->L[0] * p->L[1] * p->L[2];
+    const int slots = p->num_sms * p->ctas[precision == HSMA_FP64 ? 0 : 1];
+    const int ntb_mon = (p->nmon + TB - 1) / TB;
+    double work = 0.0;
+    std::vector<double> ns_est(nsys);
+    for (int s = 0; s < nsys; ++s) {
+        ns_est[s] = std::max(1.0, std::min((double)n[s] * p->nshifts, (double)n[s] * vsphere / vbox));
+        int ntb = (int)((n[s] + TB - 1) / TB) + ntb_mon;
+        work += (double)ntb * ns_est[s];
+    }
+    const double items_wanted = 24.0 * slots;
+    const double chunk = std::max(4.0 * tile, work / items_wanted);
+    long long part = 0, src = 0, tgt = 0, rec = 0, cnt = 0;
+    long long items = 0, surf = 0;
+    int nblk_max = 1;
+    long long max_tgt = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SysDesc &d = sh->sys[s];
+        d.n = n[s];
+        d.part_off = part;
+        d.src_off = src;
+        d.tgt_off = tgt;
+        d.nblk = (int)((n[s] + kInsetBlock - 1) / kInsetBlock);
+        d.cnt_off = cnt;
+        d.ntb_part = (int)((n[s] + TB - 1) / TB);
+        d.ntb = d.ntb_part + ntb_mon;
+        long long maxchunks = std::max(1LL, (long long)(ns_est[s] / tile));
+        d.nchunks = (int)std::max(1LL, std::min(maxchunks, (long long)llround(ns_est[s] / chunk)));
+        d.partial_off = rec;
+        d.item_off = (int)items;
+        d.surf_off = (int)surf;
+        long long ntgt = n[s] + p->nmon;
+        part += n[s];
+        src += n[s] * p->nshifts;
+        tgt += ntgt;
+        rec += (long long)d.nchunks * ntgt;
+        cnt += (long long)p->nshifts * d.nblk;
+        items += (long long)d.ntb * d.nchunks;
+        surf += (n[s] + STB - 1) / STB;
+        nblk_max = std::max(nblk_max, d.nblk);
+        max_tgt = std::max(max_tgt, ntgt);
+    }
+    sh->n_total = part;
+    sh->cap_total = src;
+    sh->tgt_total = tgt;
+    sh->rec_total = rec;
+    sh->cnt_total = cnt;
+    sh->items = (int)items;
+    sh->surf_items = (int)surf;
+    sh->nblk_max = nblk_max;
+    sh->max_tgt = max_tgt;
+}
+
+// Carve the workspace; with base == nullptr only computes the size.
+size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision, bool stage_in, bool stage_out,
+                       void *base, Workspace *w)
+{
+    Carver c(base);
+    w->xyz = stage_in ? c.take<double>(3 * sh.n_total) : nullptr;
+    w->q = stage_in ? c.take<double>(sh.n_total) : nullptr;
+    w->forces = stage_out ? c.take<double>(3 * sh.n_total) : nullptr;
+    w->pot = stage_out ? c.take<double>(sh.n_total) : nullptr;
+    if (precision == HSMA_FP64) {
+        w->src64 = c.take<double4_32a>(sh.cap_total);
+        w->src_hi = w->src_lo = nullptr;
+    } else {
+        w->src_hi = c.take<float4>(sh.cap_total);
+        w->src_lo = c.take<float4>(sh.cap_total);
+        w->src64 = nullptr;
+    }
+    w->counts = c.take<int>(sh.cnt_total);
+    w->ns = c.take<long long>(sh.nsys);
+    w->partials = c.take<float4>(2 * sh.rec_total);
+    w->phi_tgt = c.take<double>(sh.tgt_total);
+    w->e_part = c.take<double>(3 * sh.tgt_total);
+    w->b = c.take<double>((size_t)sh.nsys * p->K);
+    w->A = c.take<double>((size_t)sh.nsys * p->Nb);
+    w->img = c.take<double2>((size_t)sh.nsys * p->ndir);
+    w->phi_out = c.take<double>(sh.n_total);
+    w->e_out = c.take<double>(3 * sh.n_total);
+    w->energy = c.take<double>(sh.nsys);
+    w->status = c.take<int>(sh.nsys);
+    w->ctrl = c.take<int>(8);
+    w->sys = c.take<SysDesc>(sh.nsys);
+    w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys))
+                                                  : nullptr;
+    return align_up(c.off, 256);
+}
+
+int ensure_workspace(hsma_plan_s *p, size_t bytes)
+{
+    if (bytes <= p->ws_cap) return HSMA_OK;
+    if (p->ws_mem) {
+        HSMA_CUDA_TRY(cudaStreamSynchronize(p->stream));
+        cudaFree(p->ws_mem);
+    }
+    p->ws_mem = nullptr;
+    p->ws_cap = 0;
+    size_t nb = align_up(bytes + bytes / 8, 1 << 20);
+    cudaError_t e = cudaMalloc(&p->ws_mem, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&p->ws_mem, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p->ws_mem = nullptr;
+            return HSMA_E_OOM;
+        }
+        nb = bytes;
+    }
+    p->ws_cap = nb;
+    return HSMA_OK;
+}
+
+double host_norm(int n, int m)
+{
+    // sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!)
+    double r = 1.0;
+    for (int t = n - m + 1; t <= n + m; ++t) r /= (double)t;
+    return sqrt((m == 0 ? 1.0 : 2.0) * (2.0 * n + 1.0) / (4.0 * kPi) * r);
+}
+
+std::vector<double> norm_table(int P)
+{
+    std::vector<double> v((P + 1) * (P + 1));
+    for (int n = 0; n <= P; ++n)
+        for (int m = -n; m <= n; ++m) v[n * n + n + m] = host_norm(n, abs(m));
+    return v;
+}
+
+void record(hsma_plan_s *p, int i)
+{
+    if (p->profile && p->events_ready) cudaEventRecord(p->ev[i], p->stream);
+}
+
+// The update step for a batch of systems sharing the plan.
+int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_particles *all, double *energies,
+               double *forces, double *pot, int *status_out, hsma_out *single)
+{
+    if (!p || nsys < 1 || !offsets || !all || !all->xyz || !all->q) return HSMA_E_ARG;
+    if (offsets[0] != 0) return HSMA_E_ARG;
+    if (((uintptr_t)all->xyz | (uintptr_t)all->q | (uintptr_t)forces | (uintptr_t)pot) & 7) return HSMA_E_ARG;
+    std::vector<long long> n(nsys);
+    for (int s = 0; s < nsys; ++s) {
+        n[s] = offsets[s + 1] - offsets[s];
+        if (n[s] < 1) return HSMA_E_ARG;
+    }
+    const int prec = p->precision;
+    const bool on_dev = all->on_device != 0;
+    BatchShape sh;
+    shape_batch(p, nsys, n.data(), prec, &sh);
+    if (sh.items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
+    Workspace w;
+    size_t need = carve_workspace(p, sh, prec, !on_dev, !on_dev, nullptr, &w);
+    int rc = ensure_workspace(p, need);
+    if (rc) return rc;
+    carve_workspace(p, sh, prec, !on_dev, !on_dev, p->ws_mem, &w);
+    p->ws = w;
+    const size_t sys_bytes = align_up(sizeof(SysDesc) * nsys, 64);
+    const size_t pin_bytes = sys_bytes + align_up(sizeof(double) * nsys, 64) + align_up(sizeof(long long) * nsys, 64) +
+                             align_up(sizeof(int) * nsys, 64);
+    rc = ensure_pinned(p, pin_bytes);
+    if (rc) return rc;
+    SysDesc *hsys = (SysDesc *)p->hpin;
+    double *h_energy = (double *)((char *)p->hpin + sys_bytes);
+    long long *h_ns = (long long *)((char *)h_energy + align_up(sizeof(double) * nsys, 64));
+    int *h_status = (int *)((char *)h_ns + align_up(sizeof(long long) * nsys, 64));
+    memcpy(hsys, sh.sys.data(), sizeof(SysDesc) * nsys);
+    cudaStream_t st = p->stream;
+
+    record(p, 0);
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.sys, hsys, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, st));
+    const double *xyz = all->xyz, *q = all->q;
+    if (!on_dev) {
+        HSMA_CUDA_TRY(cudaMemcpyAsync(w.xyz, all->xyz, sizeof(double) * 3 * sh.n_total, cudaMemcpyHostToDevice, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(w.q, all->q, sizeof(double) * sh.n_total, cudaMemcpyHostToDevice, st));
+        xyz = w.xyz;
+        q = w.q;
+    }
+    HSMA_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int) * nsys, st));
+    HSMA_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
+
+    // (a1) in-set
+    InsetArgs ia;
+    ia.sys = w.sys;
+    ia.nsys = nsys;
+    ia.nblk_max = sh.nblk_max;
+    ia.xyz = xyz;
+    ia.q = q;
+    ia.shifts = p->shifts;
+    ia.n_shifts = p->nshifts;
+    for (int a = 0; a < 3; ++a) ia.g.L[a] = p->L[a];
+    ia.g.Rs = p->Rs;
+    ia.g.bc = p->bc;
+    ia.counts = w.counts;
+    ia.ns = w.ns;
+    ia.src_hi = w.src_hi;
+    ia.src_lo = w.src_lo;
+    ia.src64 = w.src64;
+    ia.status = w.status;
+    if ((rc = launch_inset(ia, st))) return rc;
+    record(p, 1);
+
+    // (a2) near-field sums at particles and monitoring targets
+    PairArgs pa;
+    pa.sys = w.sys;
+    pa.nsys = nsys;
+    pa.total_items = sh.items;
+    pa.ns = w.ns;
+    pa.src_hi = w.src_hi;
+    pa.src_lo = w.src_lo;
+    pa.src64 = w.src64;
+    pa.ext_hi = p->mon_hi;
+    pa.ext_lo = p->mon_lo;
+    pa.ext64 = p->mon64;
+    pa.n_ext = p->nmon;
+    pa.ext_field = 0;
+    pa.ext_skip_zero = 0;
+    pa.partials = w.partials;
+    pa.next_item = w.ctrl;
+    pa.status = w.status;
+    const int ctas = p->ctas[prec == HSMA_FP64 ? 0 : 1];
+    const int grid = std::max(1, std::min(sh.items, p->num_sms * ctas));
+    if ((rc = launch_pair(pa, prec, grid, st))) return rc;
+    record(p, 2);
+    if ((rc = launch_partial_reduce(w.sys, nsys, sh.max_tgt, p->nmon, w.partials, prec, w.phi_tgt, w.e_part, st)))
+        return rc;
+    record(p, 3);
+
+    // (c) fit
+    if (prec == HSMA_FP32_TC_FIT)
+        rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt, w.b,
+                           w.A, w.tc_work, st);
+    else
+        rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, w.b, w.A, st);
+    if (rc) return rc;
+    record(p, 4);
+
+    // (d) surface images and their sums at the particles
+    if ((rc = launch_surface_charges(nsys, p->ndir, p->Nb, p->Bq, p->dirs, w.A, p->Rs, w.img, st))) return rc;
+    record(p, 5);
+    if ((rc = launch_surface_pairs(w.sys, nsys, sh.surf_items, w.ns, w.src_hi, w.src_lo, w.src64, p->ndir, p->dirs,
+                                   w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st)))
+        return rc;
+    record(p, 6);
+    double *f_dst = on_dev ? forces : (forces ? w.forces : nullptr);
+    double *p_dst = on_dev ? pot : (pot ? w.pot : nullptr);
+    if ((rc = launch_finalize(w.sys, nsys, q, w.phi_tgt, w.e_part, w.phi_out, w.e_out, f_dst, p_dst, w.energy,
+                              w.status, st)))
+        return rc;
+    record(p, 7);
+    HSMA_CUDA_TRY(cudaMemcpyAsync(h_energy, w.energy, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(h_status, w.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(h_ns, w.ns, sizeof(long long) * nsys, cudaMemcpyDeviceToHost, st));
+    if (!on_dev && forces)
+        HSMA_CUDA_TRY(cudaMemcpyAsync(forces, w.forces, sizeof(double) * 3 * sh.n_total, cudaMemcpyDeviceToHost, st));
+    if (!on_dev && pot)
+        HSMA_CUDA_TRY(cudaMemcpyAsync(pot, w.pot, sizeof(double) * sh.n_total, cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+    HSMA_CUDA_TRY(cudaGetLastError());
+
+    if (p->profile && p->events_ready) {
+        const int from[8] = {0, 1, 2, 3, 4, 5, 6, 0};
+        const int to[8] = {1, 2, 3, 4, 5, 6, 7, 7};
+        for (int i = 0; i < 8; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->ev[from[i]], p->ev[to[i]]);
+            p->last_ms[i] = ms;
+        }
+        p->have_timings = true;
+    }
+    p->last_nsys = nsys;
+    p->last_n = sh.n_total;
+    p->last_shape = sh;
+
+    int worst = HSMA_OK;
+    for (int s = 0; s < nsys; ++s) {
+        if (energies) energies[s] = h_energy[s];
+        int code = map_status(h_status[s]);
+        if (status_out) status_out[s] = code;
+        if (code != HSMA_OK && worst == HSMA_OK) worst = code;
+    }
+    if (single) {
+        single->energy = h_energy[0];
+        single->n_inset = h_ns[0];
+        single->n_images = 6 * (p->F2 + 1);
+    }
+    return worst;
+}
+
+std::mutex g_scratch_mu;
+
+}  // namespace
+
+extern "C" {
+
+int hsma_opts_default(hsma_opts *o)
+{
+    if (!o) return HSMA_E_ARG;
+    memset(o, 0, sizeof(*o));
+    o->precision = HSMA_FP32_ACC64;
+    o->dr_rel = 0.0;
+    o->fib_F2 = 0;
+    o->reserved0 = 0;
+    o->stream = nullptr;
+    o->use_graphs = 1;
+    o->profile = 0;
+    return HSMA_OK;
+}
+
+const char *hsma_version(void) { return "hsma-gb300 0.1 (sm_103a)"; }
+
+const char *hsma_strerror(int code)
+{
+    switch (code) {
+        case HSMA_OK: return "ok";
+        case HSMA_E_ARG: return "invalid argument";
+        case HSMA_E_NONNEUTRAL: return "periodic system is not charge neutral";
+        case HSMA_E_OUT_OF_BOX: return "particle outside the grounded box, on a wall, or not finite";
+        case HSMA_E_COINCIDENT: return "coincident charges (non-finite result)";
+        case HSMA_E_OOM: return "out of memory";
+        case HSMA_E_TIMEOUT: return "bounded device wait timed out";
+        case HSMA_E_CUDA: return g_cuda_err[0] ? g_cuda_err : "CUDA error";
+        case HSMA_E_ILLCOND: return "fitting matrix is numerically rank deficient";
+        case HSMA_E_NOT_FOUND: return "not found";
+        case HSMA_E_AGAIN: return "not ready";
+        case HSMA_E_CAPACITY: return "request exceeds the memory budget";
+        default: return "unknown error";
+    }
+}
+
+int64_t hsma_kernel_launches(void) { return g_launches.load(); }
+
+int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, int Q, int Kmon, const hsma_opts *opts)
+{
+    if (!out || !box) return HSMA_E_ARG;
+    *out = nullptr;
+    hsma_opts o;
+    hsma_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0)) return HSMA_E_ARG;
+    if (bc != HSMA_BC_PERIODIC && bc != HSMA_BC_GROUNDED) return HSMA_E_ARG;
+    if (p < 1 || p > 40) return HSMA_E_ARG;
+    if (o.precision < 0 || o.precision > 2) return HSMA_E_ARG;
+    const double R0 = 0.5 * sqrt(box[0] * box[0] + box[1] * box[1] + box[2] * box[2]);
+    if (!(R > R0) || !isfinite(R)) return HSMA_E_ARG;
+    const int Nb = (p + 1) * (p + 1);
+    const int ncols = (bc == HSMA_BC_PERIODIC) ? Nb - 1 : Nb;
+    if (Kmon < ncols || Kmon > 16384) return HSMA_E_ARG;
+    int F2 = 0, F1 = 0;
+    if (o.fib_F2 > 0) {
+        F2 = o.fib_F2;
+        if (!fib_pred(F2, &F1) || F2 < 2) return HSMA_E_ARG;
+    } else {
+        if (Q < 12) return HSMA_E_ARG;
+        fib_from_q(Q, &F2, &F1);
+    }
+
+    hsma_plan_s *pl = new hsma_plan_s();
+    for (int a = 0; a < 3; ++a) pl->L[a] = box[a];
+    pl->bc = bc;
+    pl->P = p;
+    pl->Nb = Nb;
+    pl->ncols = ncols;
+    pl->K = Kmon;
+    pl->mon_faces = (bc == HSMA_BC_GROUNDED) ? 1 : 0;
+    pl->nmon = (bc == HSMA_BC_PERIODIC) ? 2 * Kmon : Kmon;
+    pl->F2 = F2;
+    pl->F1 = F1;
+    pl->ndir = 2 * (F2 + 1);
+    pl->Rs = R;
+    pl->R0 = R0;
+    pl->alpha = R / R0;
+    double dr_rel = o.dr_rel > 0 ? o.dr_rel : (bc == HSMA_BC_PERIODIC ? 1e-5 : 1e-4);
+    pl->dr = dr_rel * R;
+    pl->precision = o.precision;
+    pl->use_graphs = o.use_graphs;
+    pl->profile = o.profile;
+    pl->stream = (cudaStream_t)o.stream;
+
+    int rc = HSMA_OK;
+    auto fail = [&](int code) {
+        hsma_plan_destroy(pl);
+        return code;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HSMA_E_CUDA);
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return fail(HSMA_E_CUDA);
+    pl->num_sms = prop.multiProcessorCount;
+    pl->ctas[0] = pair_max_ctas_per_sm(HSMA_FP64);
+    pl->ctas[1] = pl->ctas[2] = pair_max_ctas_per_sm(HSMA_FP32_ACC64);
+
+    // image shift table: k = 0 first, then lexicographic (kx, ky, kz)
+    int Ks[3];
+    for (int a = 0; a < 3; ++a) Ks[a] = shells(R, box[a]);
+    std::vector<int4> sh;
+    sh.push_back(make_int4(0, 0, 0, 0));
+    for (int kx = -Ks[0]; kx <= Ks[0]; ++kx)
+        for (int ky = -Ks[1]; ky <= Ks[1]; ++ky)
+            for (int kz = -Ks[2]; kz <= Ks[2]; ++kz) {
+                if (!kx && !ky && !kz) continue;
+                sh.push_back(make_int4(kx, ky, kz, (abs(kx) + abs(ky) + abs(kz)) & 1));
+            }
+    pl->nshifts = (int)sh.size();
+
+    // plan memory
+    const int K = Kmon, nmon = pl->nmon, ndir = pl->ndir;
+    Carver c(nullptr);
+    for (int pass = 0; pass < 2; ++pass) {
+        c = Carver(pl->plan_mem);
+        pl->mon64 = c.take<double4_32a>(nmon);
+        pl->mon_hi = c.take<float4>(nmon);
+        pl->mon_lo = c.take<float4>(nmon);
+        pl->Mrow = c.take<double>((size_t)K * ncols);
+        pl->Mp = c.take<double>((size_t)ncols * K);
+        pl->dirs = c.take<double4_32a>(ndir);
+        pl->Bq = c.take<double>((size_t)ndir * Nb);
+        pl->norm = c.take<double>(Nb);
+        pl->shifts = c.take<int4>(sh.size());
+        pl->tc_hi = c.take<char>(tc_operand_bytes(K, ncols));
+        pl->tc_lo = c.take<char>(tc_operand_bytes(K, ncols));
+        if (pass == 0) {
+            if (cudaMalloc(&pl->plan_mem, align_up(c.off, 256)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(HSMA_E_OOM);
+            }
+        }
+    }
+    // temporaries for the basis at monitoring points and the column-major M
+    double *Bx = nullptr, *Mcol = nullptr;
+    size_t tmp_bytes = sizeof(double) * ((size_t)nmon * Nb + (size_t)K * ncols);
+    if (cudaMalloc(&Bx, tmp_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HSMA_E_OOM);
+    }
+    Mcol = Bx + (size_t)nmon * Nb;
+    cudaStream_t st = pl->stream;
+    auto nt = norm_table(p);
+    int rank_ok = 1;
+    double cond = 0.0;
+    do {
+        if (cudaMemcpyAsync(pl->norm, nt.data(), sizeof(double) * Nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(pl->shifts, sh.data(), sizeof(int4) * sh.size(), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess) {
+            rc = HSMA_E_CUDA;
+            break;
+        }
+        if (!pl->mon_faces) {
+            rc = launch_monitor_sphere(K, R0, box, pl->mon64, pl->mon_hi, pl->mon_lo, st);
+        } else {
+            // K points over the six faces in proportion to area (largest remainder)
+            double area[6], tot = 0;
+            for (int f = 0; f < 6; ++f) {
+                int a = f / 2;
+                area[f] = box[(a + 1) % 3] * box[(a + 2) % 3];
+                tot += area[f];
+            }
+            int cnt[6], used = 0;
+            double frac[6];
+            for (int f = 0; f < 6; ++f) {
+                double quota = K * area[f] / tot;
+                cnt[f] = (int)floor(quota);
+                frac[f] = quota - cnt[f];
+                used += cnt[f];
+            }
+            while (used < K) {
+                int best = 0;
+                for (int f = 1; f < 6; ++f)
+                    if (frac[f] > frac[best]) best = f;
+                cnt[best]++;
+                frac[best] = -1.0;
+                used++;
+            }
+            rc = launch_monitor_faces(cnt, box, pl->mon64, pl->mon_hi, pl->mon_lo, st);
+        }
+        if (rc) break;
+        // basis at the monitoring targets (stride 4 doubles per point)
+        if ((rc = launch_basis(p, R, nmon, (const double *)pl->mon64, 4, pl->norm, Bx, Nb, st))) break;
+        const double *Bxt = (bc == HSMA_BC_PERIODIC) ? Bx + (size_t)K * Nb : nullptr;
+        if ((rc = launch_fitting_matrix(K, Nb, ncols, bc == HSMA_BC_PERIODIC ? 1 : 0, Bx, Bxt, Mcol, pl->Mrow, st)))
+            break;
+        if ((rc = build_pseudo_inverse(K, ncols, Mcol, pl->Mp, &cond, &rank_ok, st))) break;
+        if ((rc = launch_quadrature(F2, F1, R, pl->dirs, st))) break;
+        // basis at Rs u_j == basis of the unit vector u_j with unit radius
+        if ((rc = launch_basis(p, 1.0, ndir, (const double *)pl->dirs, 4, pl->norm, pl->Bq, Nb, st))) break;
+        if ((rc = prepare_tc_operands(K, ncols, pl->Mp, pl->tc_hi, pl->tc_lo, st))) break;
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = HSMA_E_CUDA;
+            break;
+        }
+    } while (0);
+    cudaFree(Bx);
+    if (rc) return fail(rc);
+    pl->cond = cond;
+    if (!rank_ok || !(cond < 1e15)) return fail(HSMA_E_ILLCOND);
+    if (pl->profile) {
+        for (int i = 0; i < 8; ++i)
+            if (cudaEventCreate(&pl->ev[i]) != cudaSuccess) return fail(HSMA_E_CUDA);
+        pl->events_ready = true;
+    }
+    *out = pl;
+    return HSMA_OK;
+}
+
+void hsma_plan_destroy(hsma_plan_t pl)
+{
+    if (!pl) return;
+    if (pl->stream || pl->ws_mem || pl->plan_mem) cudaStreamSynchronize(pl->stream);
+    if (pl->events_ready)
+        for (int i = 0; i < 8; ++i) cudaEventDestroy(pl->ev[i]);
+    if (pl->ws_mem) cudaFree(pl->ws_mem);
+    if (pl->plan_mem) cudaFree(pl->plan_mem);
+    if (pl->hpin) cudaFreeHost(pl->hpin);
+    cudaGetLastError();
+    delete pl;
+}
+
+int hsma_plan_get_info(hsma_plan_t pl, hsma_plan_info_t *info)
+{
+    if (!pl || !info) return HSMA_E_ARG;
+    info->bc = pl->bc;
+    info->p = pl->P;
+    info->n_basis = pl->Nb;
+    info->n_cols = pl->ncols;
+    info->Kmon = pl->K;
+    info->n_mon_targets = pl->nmon;
+    info->F2 = pl->F2;
+    info->F1 = pl->F1;
+    info->n_images = 6 * (pl->F2 + 1);
+    info->n_shifts = pl->nshifts;
+    info->Rs = pl->Rs;
+    info->R0 = pl->R0;
+    info->alpha = pl->alpha;
+    info->dr = pl->dr;
+    info->cond_estimate = pl->cond;
+    info->precision = pl->precision;
+    return HSMA_OK;
+}
+
+int hsma_plan_set_stream(hsma_plan_t pl, void *stream)
+{
+    if (!pl) return HSMA_E_ARG;
+    cudaStreamSynchronize(pl->stream);
+    pl->stream = (cudaStream_t)stream;
+    return HSMA_OK;
+}
+
+int hsma_plan_set_precision(hsma_plan_t pl, int precision)
+{
+    if (!pl || precision < 0 || precision > 2) return HSMA_E_ARG;
+    pl->precision = precision;
+    return HSMA_OK;
+}
+
+int hsma_plan_footprint(hsma_plan_t pl, int64_t n, size_t *bytes)
+{
+    if (!pl || !bytes || n < 1) return HSMA_E_ARG;
+    BatchShape sh;
+    long long nn = n;
+    shape_batch(pl, 1, &nn, pl->precision, &sh);
+    Workspace w;
+    *bytes = carve_workspace(pl, sh, pl->precision, true, true, nullptr, &w);
+    return HSMA_OK;
+}
+
+int hsma_plan_get_matrix(hsma_plan_t pl, int which, double *host_out, int64_t count)
+{
+    if (!pl || !host_out) return HSMA_E_ARG;
+    std::vector<double> tmp;
+    const void *src = nullptr;
+    size_t nd = 0;
+    switch (which) {
+        case 0: nd = (size_t)pl->nmon * 4; src = pl->mon64; break;
+        case 1: nd = (size_t)pl->K * pl->ncols; src = pl->Mrow; break;
+        case 2: nd = (size_t)pl->ncols * pl->K; src = pl->Mp; break;
+        case 3:
+        case 4: nd = (size_t)pl->ndir * 4; src = pl->dirs; break;
+        case 5: nd = (size_t)pl->ndir * pl->Nb; src = pl->Bq; break;
+        default: return HSMA_E_ARG;
+    }
+    tmp.resize(nd);
+    HSMA_CUDA_TRY(cudaStreamSynchronize(pl->stream));
+    HSMA_CUDA_TRY(cudaMemcpy(tmp.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost));
+    if (which == 0 || which == 3) {
+        size_t np = nd / 4;
+        if ((int64_t)(np * 3) > count) return HSMA_E_ARG;
+        for (size_t i = 0; i < np; ++i)
+            for (int a = 0; a < 3; ++a) host_out[3 * i + a] = tmp[4 * i + a];
+    } else if (which == 4) {
+        size_t np = nd / 4;
+        if ((int64_t)np > count) return HSMA_E_ARG;
+        for (size_t i = 0; i < np; ++i) host_out[i] = tmp[4 * i + 3];
+    } else {
+        if ((int64_t)nd > count) return HSMA_E_ARG;
+        memcpy(host_out, tmp.data(), nd * sizeof(double));
+    }
+    return HSMA_OK;
+}
+
+int hsma_energy_forces(hsma_plan_t pl, const hsma_particles *x, hsma_out *out)
+{
+    if (!pl || !x || !out || x->n < 1) return HSMA_E_ARG;
+    int64_t off[2] = {0, x->n};
+    double e = 0.0;
+    int rc = run_update(pl, 1, off, x, &e, out->forces, out->potentials, nullptr, out);
+    return rc;
+}
+
+int hsma_energy_forces_batched(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_particles *all,
+                               double *energies, double *forces, double *potentials, int *status)
+{
+    if (!pl || !all || nsys < 1 || !energies) return HSMA_E_ARG;
+    for (int s = 0; s < nsys; ++s)
+        if (offsets[s + 1] <= offsets[s]) return HSMA_E_ARG;
+    if (all->n != 0 && all->n != offsets[nsys]) return HSMA_E_ARG;
+    return run_update(pl, nsys, offsets, all, energies, forces, potentials, status, nullptr);
+}
+
+int hsma_last_timings(hsma_plan_t pl, double *ms, int n)
+{
+    if (!pl || !ms || n < 0) return HSMA_E_ARG;
+    if (!pl->have_timings) return 0;
+    int k = std::min(n, 8);
+    for (int i = 0; i < k; ++i) ms[i] = pl->last_ms[i];
+    return k;
+}
+
+int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count)
+{
+    if (!pl || !host_out || pl->last_nsys < 1) return HSMA_E_ARG;
+    const SysDesc &sd = pl->last_shape.sys[0];
+    const double *src = nullptr;
+    int64_t nd = 0;
+    switch (which) {
+        case 0: src = pl->ws.A; nd = pl->Nb; break;
+        case 1: src = pl->ws.b; nd = pl->K; break;
+        case 2: src = pl->ws.phi_tgt + sd.tgt_off + sd.n; nd = pl->nmon; break;
+        case 3: src = pl->ws.phi_tgt + sd.tgt_off; nd = sd.n; break;
+        case 4: src = pl->ws.phi_out + sd.part_off; nd = sd.n; break;
+        default: return HSMA_E_ARG;
+    }
+    if (nd > count) return HSMA_E_ARG;
+    HSMA_CUDA_TRY(cudaStreamSynchronize(pl->stream));
+    HSMA_CUDA_TRY(cudaMemcpy(host_out, src, nd * sizeof(double), cudaMemcpyDeviceToHost));
+    return nd;
+}
+
+// -------------------------------------------------------------- direct sums
+namespace {
+__global__ void split_sources_kernel(long long n, const double *src, float4 *hi, float4 *lo)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float hx, lx, hy, ly, hz, lz;
+    split_f64(src[4 * i], hx, lx);
+    split_f64(src[4 * i + 1], hy, ly);
+    split_f64(src[4 * i + 2], hz, lz);
+    hi[i] = make_float4(hx, hy, hz, (float)src[4 * i + 3]);
+    lo[i] = make_float4(lx, ly, lz, 0.f);
+}
+
+__global__ void split_targets_kernel(long long n, const double *tgt, float4 *hi, float4 *lo, double4_32a *t64)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = tgt[3 * i], y = tgt[3 * i + 1], z = tgt[3 * i + 2];
+    t64[i] = make_double4_32a(x, y, z, 0.0);
+    float hx, lx, hy, ly, hz, lz;
+    split_f64(x, hx, lx);
+    split_f64(y, hy, ly);
+    split_f64(z, hz, lz);
+    hi[i] = make_float4(hx, hy, hz, 0.f);
+    lo[i] = make_float4(lx, ly, lz, 0.f);
+}
+
+__global__ void scatter_results_kernel(long long n, const double *phi, const double *e, double *pot, double *field)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pot[i] = phi[i];
+    if (field) {
+        field[3 * i] = e[3 * i];
+        field[3 * i + 1] = e[3 * i + 1];
+        field[3 * i + 2] = e[3 * i + 2];
+    }
+}
+}  // namespace
+
+int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tgt, double *pot, double *field,
+                     int precision, void *stream)
+{
+    if (ns < 1 || nt < 1 || !src || !tgt || !pot) return HSMA_E_ARG;
+    if (precision != HSMA_FP64 && precision != HSMA_FP32_ACC64) return HSMA_E_ARG;
+    if (ns > (1LL << 31) || nt > (1LL << 30)) return HSMA_E_ARG;
+    if (((uintptr_t)src | (uintptr_t)tgt | (uintptr_t)pot | (uintptr_t)field) & 7) return HSMA_E_ARG;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    HSMA_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+    const int TB = pair_targets_per_block(precision);
+    const int tile = precision == HSMA_FP64 ? 256 : 512;
+    const int ctas = pair_max_ctas_per_sm(precision);
+    const int slots = prop.multiProcessorCount * ctas;
+    SysDesc d{};
+    d.n = 0;
+    d.ntb_part = 0;
+    d.ntb = (int)((nt + TB - 1) / TB);
+    double chunk = std::max(4.0 * tile, (double)d.ntb * ns / (24.0 * slots));
+    long long maxchunks = std::max(1LL, (long long)((ns + tile - 1) / tile));
+    d.nchunks = (int)std::max(1LL, std::min(maxchunks, (long long)llround(ns / chunk)));
+    long long items = (long long)d.ntb * d.nchunks;
+    if (items > (1LL << 30)) return HSMA_E_ARG;
+    // sizes
+    size_t bytes = 0;
+    {
+        Carver cc(nullptr);
+        cc.take<float4>(ns);
+        cc.take<float4>(ns);
+        cc.take<double4_32a>(ns);
+        cc.take<float4>(nt);
+        cc.take<float4>(nt);
+        cc.take<double4_32a>(nt);
+        cc.take<float4>(2 * (size_t)d.nchunks * nt);
+        cc.take<double>(nt);
+        cc.take<double>(3 * nt);
+        cc.take<long long>(1);
+        cc.take<int>(8);
+        cc.take<int>(1);
+        cc.take<SysDesc>(1);
+        bytes = align_up(cc.off, 256);
+    }
+    void *mem = nullptr;
+    HSMA_CUDA_TRY(cudaMalloc(&mem, bytes));
+    Carver cc(mem);
+    float4 *shi = cc.take<float4>(ns);
+    float4 *slo = cc.take<float4>(ns);
+    double4_32a *s64 = cc.take<double4_32a>(ns);
+    float4 *thi = cc.take<float4>(nt);
+    float4 *tlo = cc.take<float4>(nt);
+    double4_32a *t64 = cc.take<double4_32a>(nt);
+    float4 *partials = cc.take<float4>(2 * (size_t)d.nchunks * nt);
+    double *phi = cc.take<double>(nt);
+    double *e = cc.take<double>(3 * nt);
+    long long *dns = cc.take<long long>(1);
+    int *ctrl = cc.take<int>(8);
+    int *status = cc.take<int>(1);
+    SysDesc *dsys = cc.take<SysDesc>(1);
+    int rc = HSMA_OK;
+    long long nsl = ns;
+    do {
+        if (cudaMemcpyAsync(dsys, &d, sizeof(d), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(dns, &nsl, sizeof(nsl), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(ctrl, 0, 8 * sizeof(int), st) != cudaSuccess ||
+            cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) {
+            rc = HSMA_E_CUDA;
+            break;
+        }
+        if (precision == HSMA_FP64 &&
+            cudaMemcpyAsync(s64, src, sizeof(double) * 4 * ns, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = HSMA_E_CUDA;
+            break;
+        }
+        if (precision != HSMA_FP64) {
+            split_sources_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(ns, src, shi, slo);
+            HSMA_LAUNCHED();
+        }
+        split_targets_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, tgt, thi, tlo, t64);
+        HSMA_LAUNCHED();
+        PairArgs pa;
+        pa.sys = dsys;
+        pa.nsys = 1;
+        pa.total_items = (int)items;
+        pa.ns = dns;
+        pa.src_hi = shi;
+        pa.src_lo = slo;
+        pa.src64 = s64;
+        pa.ext_hi = thi;
+        pa.ext_lo = tlo;
+        pa.ext64 = t64;
+        pa.n_ext = (int)nt;
+        pa.ext_field = field ? 1 : 0;
+        pa.ext_skip_zero = 1;
+        pa.partials = partials;
+        pa.next_item = ctrl;
+        pa.status = status;
+        int grid = (int)std::max(1LL, std::min(items, (long long)slots));
+        if ((rc = launch_pair(pa, precision, grid, st))) break;
+        if ((rc = launch_partial_reduce(dsys, 1, nt, (int)nt, partials, precision, phi, e, st))) break;
+        scatter_results_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, phi, e, pot, field);
+        HSMA_LAUNCHED();
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
+        int hst = 0;
+        if (!rc && cudaMemcpy(&hst, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HSMA_E_CUDA;
+        if (!rc) rc = map_status(hst);
+    } while (0);
+    cudaFree(mem);
+    if (rc == HSMA_OK && cudaGetLastError() != cudaSuccess) rc = HSMA_E_CUDA;
+    return rc;
+}
+
+int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, void *stream)
+{
+    if (p < 0 || p > 40 || !(Rs > 0) || np < 1 || !pts || !out) return HSMA_E_ARG;
+    int Nb = (p + 1) * (p + 1);
+    auto nt = norm_table(p);
+    double *dn = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    HSMA_CUDA_TRY(cudaMalloc(&dn, sizeof(double) * Nb));
+    int rc = HSMA_OK;
+    if (cudaMemcpyAsync(dn, nt.data(), sizeof(double) * Nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = HSMA_E_CUDA;
+    if (!rc) rc = launch_basis(p, Rs, np, pts, 3, dn, out, Nb, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
+    cudaFree(dn);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Internal declarations shared by the CUDA translation units of libhsma.
+// Not part of the public ABI (include/hsma.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/hsma.h"
+
+namespace hsma {
+
+// ----------------------------------------------------------------- launch
+extern std::atomic<long long> g_launches;  // kernels issued by this library
+
+#define HSMA_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) {                              \
+            hsma::set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            return (_e == cudaErrorMemoryAllocation) ? HSMA_E_OOM : HSMA_E_CUDA; \
+        }                                                     \
+    } while (0)
+
+#define HSMA_LAUNCHED() hsma::g_launches.fetch_add(1, std::memory_order_relaxed)
+
+void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Device status bits, one int per system; the host maps them to codes.
+enum : int {
+    ST_NONNEUTRAL = 1,
+    ST_OUT_OF_BOX = 2,
+    ST_COINCIDENT = 4,
+    ST_TIMEOUT = 8,
+    ST_CAPACITY = 16,
+};
+
+// ------------------------------------------------------------ batch layout
+// One record per system of a batch (a single-system call is a batch of one).
+struct SysDesc {
+    long long n;            // particles
+    long long part_off;     // first particle in the concatenated inputs/outputs
+    long long src_off;      // first in-set slot (capacity n * n_shifts)
+    long long tgt_off;      // first target slot: n particles then n_mon monitors
+    long long partial_off;  // first partial record: nchunks * (n + n_mon)
+    long long cnt_off;      // first in-set block count: n_shifts * nblk
+    int nchunks;            // source chunks of the near-field sums
+    int ntb;                // target blocks (particles, then monitors)
+    int ntb_part;           // target blocks holding particles
+    int nblk;               // in-set blocks per shift
+    int item_off;           // first near-field work item of this system
+    int surf_off;           // first surface work item of this system
+};
+
+// --------------------------------------------------------- numeric helpers
+// Error-free transformation a + b = s + e (Knuth's TwoSum), in FP32.  Used to
+// fold FP32 partial sums into a double-float (hi, lo) accumulator.
+__device__ __forceinline__ float2 df_add(float2 acc, float x)
+{
+    float s = __fadd_rn(acc.x, x);
+    float bb = __fsub_rn(s, acc.x);
+    float e = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    return make_float2(s, __fadd_rn(acc.y, e));
+}
+
+// Reciprocal square root on the special-function unit.
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Split an FP64 value into two FP32 words whose sum represents it to ~2^-48.
+__device__ __forceinline__ void split_f64(double v, float &hi, float &lo)
+{
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+// ------------------------------------------------- mbarrier / bulk copies
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completing on the mbarrier.  Both addresses
+// must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~max_cycles SM clocks
+// (and after a fixed number of polls), returning false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long max_cycles = 4000000000LL)
+{
+    long long t0 = clock64();
+    for (int it = 0; it < (1 << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > max_cycles) return false;
+    }
+    return false;
+}
+
+// Deterministic block-wide sum of doubles (blockDim.x a multiple of 32, <= 1024).
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *scratch /* >= 32 */)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    double r = (threadIdx.x < (unsigned)nw) ? scratch[threadIdx.x] : 0.0;
+    if (wid == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) scratch[0] = r;
+    __syncthreads();
+    r = scratch[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------ kernel launch interfaces
+// (defined in the .cu files; all enqueue on `st` and return HSMA_OK or a code)
+
+struct Geometry {
+    double L[3];
+    double Rs;
+    int bc;
+};
+
+// plan_kernels.cu
+int launch_monitor_sphere(int K, double R0, const double L[3], double4_32a *out64, float4 *hi, float4 *lo,
+                          cudaStream_t st);
+int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *out64, float4 *hi, float4 *lo,
+                         cudaStream_t st);
+int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st);
+int launch_basis(int P, double Rs, long long np, const double *pts, int pts_stride, const double *norm,
+                 double *out, long long ld, cudaStream_t st);
+int launch_fitting_matrix(int K, int Nb, int ncols, int drop, const double *Bx, const double *Bxt,
+                          double *Mcol, double *Mrow, cudaStream_t st);
+int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond, int *rank_ok,
+                         cudaStream_t st);
+
+// inset.cu
+struct InsetArgs {
+    const SysDesc *sys;
+    int nsys;
+    int nblk_max;
+    const double *xyz;
+    const double *q;
+    const int4 *shifts;
+    int n_shifts;
+    Geometry g;
+    int *counts;
+    long long *ns;
+    float4 *src_hi;
+    float4 *src_lo;
+    double4_32a *src64;
+    int *status;
+};
+int launch_inset(const InsetArgs &a, cudaStream_t st);
+
+// pair.cu
+struct PairArgs {
+    const SysDesc *sys;
+    int nsys;
+    int total_items;
+    const long long *ns;
+    const float4 *src_hi;
+    const float4 *src_lo;
+    const double4_32a *src64;
+    const float4 *ext_hi;   // external targets (monitoring points), shared by all systems
+    const float4 *ext_lo;
+    const double4_32a *ext64;
+    int n_ext;
+    int ext_field;          // external targets also need the field
+    int ext_skip_zero;      // skip pairs at distance exactly zero for external targets
+    float4 *partials;       // 2 x float4 (FP32) or 1 x double4_32a (FP64) per record
+    int *next_item;
+    int *status;
+};
+int launch_pair(const PairArgs &a, int precision, int grid, cudaStream_t st);
+int pair_targets_per_block(int precision);
+int pair_max_ctas_per_sm(int precision);
+int launch_partial_reduce(const SysDesc *sys, int nsys, long long max_tgt, int n_ext, const float4 *partials,
+                          int precision, double *phi_tgt, double *e_part, cudaStream_t st);
+
+// fit_surface.cu
+int launch_fit_fp64(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const double *Mp,
+                    const double *phi_tgt, double *b_out, double *A, cudaStream_t st);
+int launch_surface_charges(int nsys, int ndir, int Nb, const double *Bq, const double4_32a *dirs, const double *A,
+                           double Rs, double2 *img, cudaStream_t st);
+int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const long long *ns, const float4 *src_hi,
+                         const float4 *src_lo, const double4_32a *src64, int ndir, const double4_32a *dirs,
+                         const double2 *img, double Rs, double dr, int precision, double *phi_out,
+                         double *e_out, cudaStream_t st);
+int launch_finalize(const SysDesc *sys, int nsys, const double *q, const double *phi_tgt, const double *e_part,
+                    const double *phi_out, const double *e_out, double *forces, double *pot, double *energy,
+                    int *status, cudaStream_t st);
+
+// tc_fit.cu
+int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
+                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, double *b_out, double *A,
+                  float *work, cudaStream_t st);
+int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *Mp_lo, cudaStream_t st);
+size_t tc_operand_bytes(int K, int ncols);
+size_t tc_work_bytes(int K, int ncols, int nsys);
+
+}  // namespace hsma

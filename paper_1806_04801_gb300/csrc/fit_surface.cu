@@ -1,0 +1,357 @@
+// Fit, harmonic surface mapping and energy/forces (Sec. II.A-C).
+//
+//  fit_fp64          b from the monitoring potentials (periodic:
+//                    b_i = Phi_in(x~_i) - Phi_in(x_i); grounded: b_i = -Phi_in(x_i))
+//                    and A = M+ b (FP64 matrix-vector product per system).
+//  surface_charges   at each integration direction u_j: Phi_out(Rs u_j) and
+//                    sigma(Rs u_j) = (1/Rs) sum n A_nm B_nm(Rs u_j); the point
+//                    images carry Q_sigma = w sigma/(4 pi) at Rs u_j and the
+//                    dipole pair +-p/dr, p = w Phi_out/(4 pi), at (Rs -+ dr/2) u_j
+//                    (Eqs. "green", "cd", "integrals" and the Fibonacci rule).
+//  surface_pairs     potential and field of those images at every particle.
+//  finalize          U = 1/2 sum q_i (Phi_in + Phi_out), F_i = q_i E_i.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace hsma {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__global__ void fit_fp64_kernel(const SysDesc *sys, int bc, int K, int ncols, int Nb, const double *Mp,
+                                const double *phi_tgt, double *b_out, double *A)
+{
+    const SysDesc sd = sys[blockIdx.y];
+    const double *ph = phi_tgt + sd.tgt_off + sd.n;  // monitoring targets
+    const int drop = (bc == HSMA_BC_PERIODIC) ? 1 : 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < K; i += blockDim.x) {
+            double b = drop ? ph[K + i] - ph[i] : -ph[i];
+            b_out[(long long)blockIdx.y * K + i] = b;
+        }
+        if (drop && threadIdx.x == 0) A[(long long)blockIdx.y * Nb] = 0.0;
+    }
+    if (c >= ncols) return;
+    const double *row = Mp + (long long)c * K;
+    double s = 0.0;
+    for (int i = lane; i < K; i += 32) {
+        double b = drop ? ph[K + i] - ph[i] : -ph[i];
+        s += row[i] * b;
+    }
+    s = warp_sum(s);
+    if (lane == 0) A[(long long)blockIdx.y * Nb + c + drop] = s;
+}
+
+__device__ __forceinline__ int degree_of(int k)
+{
+    int n = (int)sqrt((double)k);
+    while (n * n > k) --n;
+    while ((n + 1) * (n + 1) <= k) ++n;
+    return n;
+}
+
+// One warp per (system, direction).
+__global__ void surface_charges_kernel(int ndir, int Nb, const double *Bq, const double4_32a *dirs, const double *A,
+                                       double Rs, double2 *img)
+{
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (d >= ndir) return;
+    const double *a = A + (long long)blockIdx.y * Nb;
+    const double *row = Bq + (long long)d * Nb;
+    double phi = 0.0, sig = 0.0;
+    for (int k = lane; k < Nb; k += 32) {
+        double v = row[k] * a[k];
+        phi += v;
+        sig += degree_of(k) * v;
+    }
+    phi = warp_sum(phi);
+    sig = warp_sum(sig);
+    if (lane == 0) {
+        double w = dirs[d].w;
+        img[(long long)blockIdx.y * ndir + d] = make_double2(w * sig / (Rs * 4.0 * kPi), w * phi / (4.0 * kPi));
+    }
+}
+
+constexpr int kSurfThreads = 128;
+constexpr int kSurfT = 2;
+constexpr int kSurfTB = kSurfThreads * kSurfT;
+constexpr int kSurfTile = 256;
+
+__device__ __forceinline__ int find_sys_surf(const SysDesc *sys, int nsys, int item)
+{
+    int lo = 0, hi = nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (sys[mid].surf_off <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// FP32 form.  For direction u with d = r - Rs u, h = dr/2, a = u.d:
+//   sigma image:  Q/|d|, field Q d/|d|^3
+//   dipole pair:  (p/dr)(1/A - 1/B) with A = |d + h u|, B = |d - h u|
+//                 = -2 p a / (A B (A + B))                  (no cancellation)
+//   its field:    (p/dr)((d + h u)/A^3 - (d - h u)/B^3)
+//                 = p [ -2 a (A^2 + A B + B^2) / ((A + B) A^3 B^3) d
+//                       + (u/2)(1/A^3 + 1/B^3) ]
+__global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
+    const SysDesc *sys, int nsys, const float4 *src_hi, const float4 *src_lo, int ndir, const double4_32a *dirs,
+    const double2 *img, float Rs, float h, double *phi_out, double *e_out)
+{
+    __shared__ float4 su[kSurfTile];   // (u_x, u_y, u_z, Q_sigma)
+    __shared__ float sp[kSurfTile];    // p
+    const int s = find_sys_surf(sys, nsys, blockIdx.x);
+    const SysDesc sd = sys[s];
+    const int blk = blockIdx.x - sd.surf_off;
+    float rx[kSurfT], ry[kSurfT], rz[kSurfT];
+    long long idx[kSurfT];
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) {
+        long long i = (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+        idx[t] = (i < sd.n) ? i : -1;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (i < sd.n) {
+            a = src_hi[sd.src_off + i];
+            b = src_lo[sd.src_off + i];
+        }
+        rx[t] = a.x + b.x;
+        ry[t] = a.y + b.y;
+        rz[t] = a.z + b.z;
+    }
+    float2 phi[kSurfT], e[kSurfT][3];
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) {
+        phi[t] = make_float2(0.f, 0.f);
+        e[t][0] = e[t][1] = e[t][2] = make_float2(0.f, 0.f);
+    }
+    const double2 *im = img + (long long)s * ndir;
+    for (int d0 = 0; d0 < ndir; d0 += kSurfTile) {
+        int cnt = min(kSurfTile, ndir - d0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += kSurfThreads) {
+            double4_32a u = dirs[d0 + j];
+            double2 c = im[d0 + j];
+            bool live = u.w > 0.0;
+            su[j] = make_float4((float)u.x, (float)u.y, (float)u.z, live ? (float)c.x : 0.f);
+            sp[j] = live ? (float)c.y : 0.f;
+        }
+        __syncthreads();
+        float pa[kSurfT], ea[kSurfT][3];
+#pragma unroll
+        for (int t = 0; t < kSurfT; ++t) pa[t] = ea[t][0] = ea[t][1] = ea[t][2] = 0.f;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 u = su[j];
+            const float p = sp[j];
+#pragma unroll
+            for (int t = 0; t < kSurfT; ++t) {
+                float dx = fmaf(-Rs, u.x, rx[t]);
+                float dy = fmaf(-Rs, u.y, ry[t]);
+                float dz = fmaf(-Rs, u.z, rz[t]);
+                float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ad = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
+                float base = fmaf(h, h, dd);
+                float A2 = fmaf(2.f * h, ad, base);
+                float B2 = fmaf(-2.f * h, ad, base);
+                float ri = rsqrt_sfu(dd);
+                float Ai = rsqrt_sfu(A2);
+                float Bi = rsqrt_sfu(B2);
+                float Aa = A2 * Ai, Bb = B2 * Bi;
+                float inv_sum = 1.f / (Aa + Bb);
+                float qs = u.w * ri;
+                float dip = -2.f * p * ad * Ai * Bi * inv_sum;
+                pa[t] += qs + dip;
+                float ri3 = ri * ri * ri;
+                float Ai3 = Ai * Ai * Ai, Bi3 = Bi * Bi * Bi;
+                float cd = u.w * ri3 - 2.f * p * ad * (A2 + Aa * Bb + B2) * inv_sum * Ai3 * Bi3;
+                float cu = 0.5f * p * (Ai3 + Bi3);
+                ea[t][0] += fmaf(cd, dx, cu * u.x);
+                ea[t][1] += fmaf(cd, dy, cu * u.y);
+                ea[t][2] += fmaf(cd, dz, cu * u.z);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSurfT; ++t) {
+            phi[t] = df_add(phi[t], pa[t]);
+            e[t][0] = df_add(e[t][0], ea[t][0]);
+            e[t][1] = df_add(e[t][1], ea[t][1]);
+            e[t][2] = df_add(e[t][2], ea[t][2]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) {
+        if (idx[t] < 0) continue;
+        long long o = sd.part_off + idx[t];
+        phi_out[o] = (double)phi[t].x + (double)phi[t].y;
+        e_out[3 * o] = (double)e[t][0].x + (double)e[t][0].y;
+        e_out[3 * o + 1] = (double)e[t][1].x + (double)e[t][1].y;
+        e_out[3 * o + 2] = (double)e[t][2].x + (double)e[t][2].y;
+    }
+}
+
+// FP64 form: the three point images of each direction summed literally.
+__global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
+    const SysDesc *sys, int nsys, const double4_32a *src64, int ndir, const double4_32a *dirs, const double2 *img,
+    double Rs, double dr, double *phi_out, double *e_out)
+{
+    __shared__ double4_32a su[kSurfTile];
+    __shared__ double sp[kSurfTile];
+    const int s = find_sys_surf(sys, nsys, blockIdx.x);
+    const SysDesc sd = sys[s];
+    const int blk = blockIdx.x - sd.surf_off;
+    double r[kSurfT][3];
+    long long idx[kSurfT];
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) {
+        long long i = (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+        idx[t] = (i < sd.n) ? i : -1;
+        double4_32a a = make_double4_32a(0, 0, 0, 0);
+        if (i < sd.n) a = src64[sd.src_off + i];
+        r[t][0] = a.x;
+        r[t][1] = a.y;
+        r[t][2] = a.z;
+    }
+    double phi[kSurfT], e[kSurfT][3];
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) phi[t] = e[t][0] = e[t][1] = e[t][2] = 0.0;
+    const double2 *im = img + (long long)s * ndir;
+    const double Rin = Rs - 0.5 * dr, Rout = Rs + 0.5 * dr;
+    for (int d0 = 0; d0 < ndir; d0 += kSurfTile) {
+        int cnt = min(kSurfTile, ndir - d0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += kSurfThreads) {
+            double4_32a u = dirs[d0 + j];
+            double2 c = im[d0 + j];
+            su[j] = make_double4_32a(u.x, u.y, u.z, c.x);
+            sp[j] = c.y / dr;
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const double4_32a u = su[j];
+            const double pd = sp[j];
+            const double R3[3] = {Rs, Rin, Rout};
+            const double Q3[3] = {u.w, pd, -pd};
+#pragma unroll
+            for (int t = 0; t < kSurfT; ++t) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    double dx = r[t][0] - R3[m] * u.x;
+                    double dy = r[t][1] - R3[m] * u.y;
+                    double dz = r[t][2] - R3[m] * u.z;
+                    double ri = rsqrt(dx * dx + dy * dy + dz * dz);
+                    double qr = Q3[m] * ri;
+                    phi[t] += qr;
+                    double qr3 = qr * ri * ri;
+                    e[t][0] += qr3 * dx;
+                    e[t][1] += qr3 * dy;
+                    e[t][2] += qr3 * dz;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kSurfT; ++t) {
+        if (idx[t] < 0) continue;
+        long long o = sd.part_off + idx[t];
+        phi_out[o] = phi[t];
+        e_out[3 * o] = e[t][0];
+        e_out[3 * o + 1] = e[t][1];
+        e_out[3 * o + 2] = e[t][2];
+    }
+}
+
+// Per system: forces, potentials and U = 1/2 sum q_i phi_i (fixed order).
+__global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, const double *q, const double *phi_tgt,
+                                                        const double *e_part, const double *phi_out,
+                                                        const double *e_out, double *forces, double *pot,
+                                                        double *energy, int *status)
+{
+    __shared__ double red[32];
+    const int s = blockIdx.x;
+    const SysDesc sd = sys[s];
+    double u = 0.0;
+    bool bad = false;
+    for (long long i = threadIdx.x; i < sd.n; i += blockDim.x) {
+        long long t = sd.tgt_off + i, o = sd.part_off + i;
+        double qi = q[o];
+        double ph = phi_tgt[t] + phi_out[o];
+        double ex = e_part[3 * t] + e_out[3 * o];
+        double ey = e_part[3 * t + 1] + e_out[3 * o + 1];
+        double ez = e_part[3 * t + 2] + e_out[3 * o + 2];
+        if (!isfinite(ph) || !isfinite(ex) || !isfinite(ey) || !isfinite(ez)) bad = true;
+        if (forces) {
+            forces[3 * o] = qi * ex;
+            forces[3 * o + 1] = qi * ey;
+            forces[3 * o + 2] = qi * ez;
+        }
+        if (pot) pot[o] = ph;
+        u += qi * ph;
+    }
+    if (bad) atomicOr(&status[s], ST_COINCIDENT);
+    u = block_sum(u, red);
+    if (threadIdx.x == 0) {
+        energy[s] = 0.5 * u;
+        if (!isfinite(u)) atomicOr(&status[s], ST_COINCIDENT);
+    }
+}
+
+}  // namespace
+
+int launch_fit_fp64(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const double *Mp,
+                    const double *phi_tgt, double *b_out, double *A, cudaStream_t st)
+{
+    dim3 grid((ncols + 7) / 8, nsys);
+    fit_fp64_kernel<<<grid, 256, 0, st>>>(sys, bc, K, ncols, Nb, Mp, phi_tgt, b_out, A);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_surface_charges(int nsys, int ndir, int Nb, const double *Bq, const double4_32a *dirs, const double *A,
+                           double Rs, double2 *img, cudaStream_t st)
+{
+    dim3 grid((ndir + 7) / 8, nsys);
+    surface_charges_kernel<<<grid, 256, 0, st>>>(ndir, Nb, Bq, dirs, A, Rs, img);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int surface_targets_per_block() { return kSurfTB; }
+
+int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const long long *ns, const float4 *src_hi,
+                         const float4 *src_lo, const double4_32a *src64, int ndir, const double4_32a *dirs,
+                         const double2 *img, double Rs, double dr, int precision, double *phi_out,
+                         double *e_out, cudaStream_t st)
+{
+    (void)ns;
+    if (total_items <= 0) return HSMA_OK;
+    if (precision == HSMA_FP64)
+        surface_pairs_fp64_kernel<<<total_items, kSurfThreads, 0, st>>>(sys, nsys, src64, ndir, dirs, img, Rs, dr,
+                                                                         phi_out, e_out);
+    else
+        surface_pairs_fp32_kernel<<<total_items, kSurfThreads, 0, st>>>(
+            sys, nsys, src_hi, src_lo, ndir, dirs, img, (float)Rs, (float)(0.5 * dr), phi_out, e_out);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_finalize(const SysDesc *sys, int nsys, const double *q, const double *phi_tgt, const double *e_part,
+                    const double *phi_out, const double *e_out, double *forces, double *pot, double *energy,
+                    int *status, cudaStream_t st)
+{
+    finalize_kernel<<<nsys, 1024, 0, st>>>(sys, q, phi_tgt, e_part, phi_out, e_out, forces, pot, energy, status);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+}  // namespace hsma

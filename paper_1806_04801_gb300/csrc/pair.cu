@@ -1,0 +1,475 @@
+// Near-field Coulomb sums (Sec. II.A: Phi_in = sum_{j <= N_s} q_j/|r_j - r|,
+// evaluated at the particles -- potential and field -- and at the monitoring
+// points -- potential).  This is the hot loop of the method (Sec. II.C: "the
+// most time-consuming calculations").
+//
+// Work decomposition: one persistent grid pulls items (system, target block,
+// source chunk) from an atomic counter.  A CTA stages the chunk's sources in
+// shared-memory tiles with 1-D bulk copies (cp.async.bulk, completion on an
+// mbarrier, two buffers in flight) and every thread sums the tile into the
+// registers of its T targets.  Each item writes one partial record per target;
+// a second kernel adds the chunks of every target in a fixed order, so results
+// do not depend on scheduling.
+//
+// FP32 form: positions are held as two FP32 words (hi + lo, the in-set kernel
+// splits the FP64 value), so the difference (y_hi - x_hi) + (y_lo - x_lo) is
+// accurate to a few FP32 ulps of the distance itself, even for the closest
+// pairs; 1/r comes from the SFU (rsqrt.approx); the potential is summed in
+// FP32 over 32 sources and the field over a whole tile, then folded into
+// double-float (hi, lo) accumulators with an error-free TwoSum.
+//
+// FP64 form: the same loop in double, rsqrt() from the CUDA math library.
+#include "common.cuh"
+
+namespace hsma {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kT32 = 4;
+constexpr int kTB32 = kThreads * kT32;  // targets per block, FP32 form
+constexpr int kTile32 = 512;            // sources per tile, FP32 form
+constexpr int kT64 = 2;
+constexpr int kTB64 = kThreads * kT64;
+constexpr int kTile64 = 256;
+constexpr int kFold = 32;               // potential fold interval (sources)
+constexpr float kFar = 1.0e4f;          // position of zero-charge padding sources
+
+struct Item {
+    int sys, tb, chunk;
+};
+
+__device__ __forceinline__ Item decode_item(const PairArgs &a, int item)
+{
+    int lo = 0, hi = a.nsys - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.sys[mid].item_off <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const SysDesc &sd = a.sys[lo];
+    int local = item - sd.item_off;
+    Item it;
+    it.sys = lo;
+    it.chunk = local / sd.ntb;
+    it.tb = local - it.chunk * sd.ntb;
+    return it;
+}
+
+// ------------------------------------------------------------ FP32 tiles
+// SKIP: 0 = no exclusion; 1 = skip the target's own slot (self_rel[t] = own
+// slot - tile start); 2 = skip pairs at distance exactly zero.
+template <bool FIELD, int SKIP>
+__device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int cnt_pad,
+                                       const float (&th)[kT32][3], const float (&tl)[kT32][3],
+                                       const int (&self_rel)[kT32], float2 (&phi)[kT32], float2 (&g)[kT32][3])
+{
+    float ga[kT32][3];
+#pragma unroll
+    for (int t = 0; t < kT32; ++t) ga[t][0] = ga[t][1] = ga[t][2] = 0.f;
+    for (int s0 = 0; s0 < cnt_pad; s0 += kFold) {
+        float pa[kT32];
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) pa[t] = 0.f;
+#pragma unroll 4
+        for (int s = 0; s < kFold; ++s) {
+            const float4 h = sh[s0 + s];
+            const float4 l = sl[s0 + s];
+#pragma unroll
+            for (int t = 0; t < kT32; ++t) {
+                float dx = (h.x - th[t][0]) + (l.x - tl[t][0]);
+                float dy = (h.y - th[t][1]) + (l.y - tl[t][1]);
+                float dz = (h.z - th[t][2]) + (l.z - tl[t][2]);
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float ri = rsqrt_sfu(r2);
+                if (SKIP == 1) ri = (s0 + s == self_rel[t]) ? 0.f : ri;
+                if (SKIP == 2) ri = (r2 > 0.f) ? ri : 0.f;
+                float qr = h.w * ri;
+                pa[t] += qr;
+                if (FIELD) {
+                    float qr3 = qr * ri * ri;
+                    ga[t][0] = fmaf(qr3, dx, ga[t][0]);
+                    ga[t][1] = fmaf(qr3, dy, ga[t][1]);
+                    ga[t][2] = fmaf(qr3, dz, ga[t][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) phi[t] = df_add(phi[t], pa[t]);
+    }
+    if (FIELD) {
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) {
+            g[t][0] = df_add(g[t][0], ga[t][0]);
+            g[t][1] = df_add(g[t][1], ga[t][1]);
+            g[t][2] = df_add(g[t][2], ga[t][2]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
+{
+    extern __shared__ __align__(128) float4 smem32[];
+    float4 *sh_hi = smem32;                // [2][kTile32]
+    float4 *sh_lo = smem32 + 2 * kTile32;  // [2][kTile32]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_item, s_abort;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.next_item, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.total_items || s_abort) break;
+        const Item it = decode_item(a, item);
+        const SysDesc sd = a.sys[it.sys];
+        const long long Ns = a.ns[it.sys];
+        const long long ntiles = (Ns + kTile32 - 1) / kTile32;
+        const int t0 = (int)(it.chunk * ntiles / sd.nchunks);
+        const int t1 = (int)((it.chunk + 1) * ntiles / sd.nchunks);
+        const bool part = it.tb < sd.ntb_part;
+        const bool field = part || a.ext_field;
+        const long long ntgt = sd.n + a.n_ext;
+
+        // targets of this thread
+        float th[kT32][3], tl[kT32][3];
+        long long tidx[kT32];
+        long long tb_lo = 0, tb_hi = 0;  // in-set slots of this block's own particles
+        if (part) {
+            tb_lo = (long long)it.tb * kTB32;
+            tb_hi = tb_lo + kTB32;
+        }
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) {
+            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * kTB32 + t * kThreads + tid;
+            bool valid = part ? (k < sd.n) : (k < a.n_ext);
+            float4 h = make_float4(kFar, kFar, kFar, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) {
+                if (part) {
+                    h = a.src_hi[sd.src_off + k];
+                    l = a.src_lo[sd.src_off + k];
+                } else {
+                    h = a.ext_hi[k];
+                    l = a.ext_lo[k];
+                }
+            }
+            th[t][0] = h.x; th[t][1] = h.y; th[t][2] = h.z;
+            tl[t][0] = l.x; tl[t][1] = l.y; tl[t][2] = l.z;
+            tidx[t] = valid ? (part ? k : sd.n + k) : -1;
+        }
+        float2 phi[kT32], g[kT32][3];
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) {
+            phi[t] = make_float2(0.f, 0.f);
+            g[t][0] = g[t][1] = g[t][2] = make_float2(0.f, 0.f);
+        }
+
+        const float4 *gh = a.src_hi + sd.src_off;
+        const float4 *gl = a.src_lo + sd.src_off;
+        const int ntile = t1 - t0;
+        auto issue = [&](int k, int buf) {
+            long long s0 = (long long)(t0 + k) * kTile32;
+            int cnt = (int)min((long long)kTile32, Ns - s0);
+            uint32_t bytes = (uint32_t)cnt * 16u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[buf], 2u * bytes);
+            bulk_g2s(sh_hi + buf * kTile32, gh + s0, bytes, &bar[buf]);
+            bulk_g2s(sh_lo + buf * kTile32, gl + s0, bytes, &bar[buf]);
+        };
+        if (tid == 0) {
+            if (ntile > 0) issue(0, 0);
+            if (ntile > 1) issue(1, 1);
+        }
+        for (int k = 0; k < ntile; ++k) {
+            const int buf = k & 1;
+            if (!mbar_wait_bounded(&bar[buf], parity[buf])) {
+                s_abort = 1;
+                atomicOr(&a.status[it.sys], ST_TIMEOUT);
+            }
+            parity[buf] ^= 1u;
+            const long long s0 = (long long)(t0 + k) * kTile32;
+            const int cnt = (int)min((long long)kTile32, Ns - s0);
+            const int cnt_pad = (cnt + kFold - 1) / kFold * kFold;
+            float4 *bh = sh_hi + buf * kTile32;
+            float4 *bl = sh_lo + buf * kTile32;
+            if (cnt_pad > cnt) {
+                for (int s = cnt + tid; s < cnt_pad; s += kThreads) {
+                    bh[s] = make_float4(kFar, -kFar, kFar, 0.f);
+                    bl[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            const int skip = part ? ((s0 < tb_hi && s0 + cnt > tb_lo) ? 1 : 0) : (a.ext_skip_zero ? 2 : 0);
+            int self_rel[kT32];
+#pragma unroll
+            for (int t = 0; t < kT32; ++t) self_rel[t] = (int)(tidx[t] - s0);
+            if (field) {
+                if (skip == 1)
+                    tile32<true, 1>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                else if (skip == 2)
+                    tile32<true, 2>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                else
+                    tile32<true, 0>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+            } else {
+                if (skip == 2)
+                    tile32<false, 2>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                else
+                    tile32<false, 0>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+            }
+            __syncthreads();
+            if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
+        }
+        if (s_abort) {
+            // give copies still in flight a bounded chance to land before exit
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bar[b], parity[b], 200000000LL);
+            break;
+        }
+        float4 *rec = a.partials + 2 * (sd.partial_off + (long long)it.chunk * ntgt);
+#pragma unroll
+        for (int t = 0; t < kT32; ++t) {
+            if (tidx[t] < 0) continue;
+            rec[2 * tidx[t]] = make_float4(phi[t].x, phi[t].y, g[t][0].x, g[t][0].y);
+            rec[2 * tidx[t] + 1] = make_float4(g[t][1].x, g[t][1].y, g[t][2].x, g[t][2].y);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ FP64 tiles
+template <bool FIELD, int SKIP>
+__device__ __forceinline__ void tile64(const double4_32a *__restrict__ s4, int cnt, const double (&tx)[kT64][3],
+                                       const int (&self_rel)[kT64], double (&phi)[kT64], double (&g)[kT64][3])
+{
+#pragma unroll 2
+    for (int s = 0; s < cnt; ++s) {
+        const double4_32a p = s4[s];
+#pragma unroll
+        for (int t = 0; t < kT64; ++t) {
+            double dx = p.x - tx[t][0];
+            double dy = p.y - tx[t][1];
+            double dz = p.z - tx[t][2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double ri = rsqrt(r2);
+            if (SKIP == 1) ri = (s == self_rel[t]) ? 0.0 : ri;
+            if (SKIP == 2) ri = (r2 > 0.0) ? ri : 0.0;
+            double qr = p.w * ri;
+            phi[t] += qr;
+            if (FIELD) {
+                double qr3 = qr * ri * ri;
+                g[t][0] += qr3 * dx;
+                g[t][1] += qr3 * dy;
+                g[t][2] += qr3 * dz;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) pair_fp64_kernel(PairArgs a)
+{
+    extern __shared__ __align__(128) double4_32a smem64[];  // [2][kTile64]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_item, s_abort;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint32_t parity[2] = {0u, 0u};
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.next_item, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.total_items || s_abort) break;
+        const Item it = decode_item(a, item);
+        const SysDesc sd = a.sys[it.sys];
+        const long long Ns = a.ns[it.sys];
+        const long long ntiles = (Ns + kTile64 - 1) / kTile64;
+        const int t0 = (int)(it.chunk * ntiles / sd.nchunks);
+        const int t1 = (int)((it.chunk + 1) * ntiles / sd.nchunks);
+        const bool part = it.tb < sd.ntb_part;
+        const bool field = part || a.ext_field;
+        const long long ntgt = sd.n + a.n_ext;
+
+        double tx[kT64][3];
+        long long tidx[kT64];
+        long long tb_lo = 0, tb_hi = 0;
+        if (part) {
+            tb_lo = (long long)it.tb * kTB64;
+            tb_hi = tb_lo + kTB64;
+        }
+#pragma unroll
+        for (int t = 0; t < kT64; ++t) {
+            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * kTB64 + t * kThreads + tid;
+            bool valid = part ? (k < sd.n) : (k < a.n_ext);
+            double4_32a p = make_double4_32a(1e4, 1e4, 1e4, 0.0);
+            if (valid) p = part ? a.src64[sd.src_off + k] : a.ext64[k];
+            tx[t][0] = p.x; tx[t][1] = p.y; tx[t][2] = p.z;
+            tidx[t] = valid ? (part ? k : sd.n + k) : -1;
+        }
+        double phi[kT64], g[kT64][3];
+#pragma unroll
+        for (int t = 0; t < kT64; ++t) phi[t] = g[t][0] = g[t][1] = g[t][2] = 0.0;
+
+        const double4_32a *gs = a.src64 + sd.src_off;
+        const int ntile = t1 - t0;
+        auto issue = [&](int k, int buf) {
+            long long s0 = (long long)(t0 + k) * kTile64;
+            int cnt = (int)min((long long)kTile64, Ns - s0);
+            uint32_t bytes = (uint32_t)cnt * 32u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[buf], bytes);
+            bulk_g2s(smem64 + buf * kTile64, gs + s0, bytes, &bar[buf]);
+        };
+        if (tid == 0) {
+            if (ntile > 0) issue(0, 0);
+            if (ntile > 1) issue(1, 1);
+        }
+        for (int k = 0; k < ntile; ++k) {
+            const int buf = k & 1;
+            if (!mbar_wait_bounded(&bar[buf], parity[buf])) {
+                s_abort = 1;
+                atomicOr(&a.status[it.sys], ST_TIMEOUT);
+            }
+            parity[buf] ^= 1u;
+            __syncthreads();
+            if (s_abort) break;
+            const long long s0 = (long long)(t0 + k) * kTile64;
+            const int cnt = (int)min((long long)kTile64, Ns - s0);
+            const double4_32a *b4 = smem64 + buf * kTile64;
+            const int skip = part ? ((s0 < tb_hi && s0 + cnt > tb_lo) ? 1 : 0) : (a.ext_skip_zero ? 2 : 0);
+            int self_rel[kT64];
+#pragma unroll
+            for (int t = 0; t < kT64; ++t) self_rel[t] = (int)(tidx[t] - s0);
+            if (field) {
+                if (skip == 1)
+                    tile64<true, 1>(b4, cnt, tx, self_rel, phi, g);
+                else if (skip == 2)
+                    tile64<true, 2>(b4, cnt, tx, self_rel, phi, g);
+                else
+                    tile64<true, 0>(b4, cnt, tx, self_rel, phi, g);
+            } else {
+                if (skip == 2)
+                    tile64<false, 2>(b4, cnt, tx, self_rel, phi, g);
+                else
+                    tile64<false, 0>(b4, cnt, tx, self_rel, phi, g);
+            }
+            __syncthreads();
+            if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
+        }
+        if (s_abort) {
+            for (int b = 0; b < 2; ++b) mbar_wait_bounded(&bar[b], parity[b], 200000000LL);
+            break;
+        }
+        double4_32a *rec = reinterpret_cast<double4_32a *>(a.partials) + (sd.partial_off + (long long)it.chunk * ntgt);
+#pragma unroll
+        for (int t = 0; t < kT64; ++t) {
+            if (tidx[t] < 0) continue;
+            rec[tidx[t]] = make_double4_32a(phi[t], g[t][0], g[t][1], g[t][2]);
+        }
+        __syncthreads();
+    }
+}
+
+// Sum the chunk partials of every target in chunk order (deterministic).
+// phi_tgt[tgt_off + t] = potential, e_part[3 (tgt_off + t) + a] = field
+// E = -sum q (y - x)/r^3.
+__global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float4 *partials, int precision,
+                                      double *phi_tgt, double *e_part)
+{
+    const SysDesc sd = sys[blockIdx.y];
+    long long ntgt = sd.n + n_ext;
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntgt) return;
+    double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    if (precision == HSMA_FP64) {
+        const double4_32a *rec = reinterpret_cast<const double4_32a *>(partials) + sd.partial_off;
+        for (int c = 0; c < sd.nchunks; ++c) {
+            double4_32a r = rec[(long long)c * ntgt + t];
+            p += r.x;
+            gx += r.y;
+            gy += r.z;
+            gz += r.w;
+        }
+    } else {
+        const float4 *rec = partials + 2 * sd.partial_off;
+        for (int c = 0; c < sd.nchunks; ++c) {
+            float4 r0 = rec[2 * ((long long)c * ntgt + t)];
+            float4 r1 = rec[2 * ((long long)c * ntgt + t) + 1];
+            p += (double)r0.x + (double)r0.y;
+            gx += (double)r0.z + (double)r0.w;
+            gy += (double)r1.x + (double)r1.y;
+            gz += (double)r1.z + (double)r1.w;
+        }
+    }
+    long long o = sd.tgt_off + t;
+    phi_tgt[o] = p;
+    e_part[3 * o] = -gx;
+    e_part[3 * o + 1] = -gy;
+    e_part[3 * o + 2] = -gz;
+}
+
+}  // namespace
+
+int pair_targets_per_block(int precision) { return precision == HSMA_FP64 ? kTB64 : kTB32; }
+
+static size_t pair_smem(int precision)
+{
+    return precision == HSMA_FP64 ? 2 * kTile64 * sizeof(double4_32a) : 4 * kTile32 * sizeof(float4);
+}
+
+int pair_max_ctas_per_sm(int precision)
+{
+    int n = 0;
+    size_t sm = pair_smem(precision);
+    if (precision == HSMA_FP64) {
+        cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel, kThreads, sm);
+    } else {
+        cudaFuncSetAttribute(pair_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp32_kernel, kThreads, sm);
+    }
+    return n > 0 ? n : 1;
+}
+
+int launch_pair(const PairArgs &a, int precision, int grid, cudaStream_t st)
+{
+    if (a.total_items <= 0) return HSMA_OK;
+    size_t sm = pair_smem(precision);
+    if (precision == HSMA_FP64) {
+        HSMA_CUDA_TRY(cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
+    } else {
+        HSMA_CUDA_TRY(cudaFuncSetAttribute(pair_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        pair_fp32_kernel<<<grid, kThreads, sm, st>>>(a);
+    }
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_partial_reduce(const SysDesc *sys, int nsys, long long max_tgt, int n_ext, const float4 *partials,
+                          int precision, double *phi_tgt, double *e_part, cudaStream_t st)
+{
+    dim3 grid((unsigned)((max_tgt + 255) / 256), nsys);
+    partial_reduce_kernel<<<grid, 256, 0, st>>>(sys, n_ext, partials, precision, phi_tgt, e_part);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+}  // namespace hsma

@@ -1,0 +1,391 @@
+// Preparation-step kernels (Sec. II.C, Table I upper half): monitoring points,
+// Fibonacci integration directions, the harmonic basis, and the FP64
+// pseudo-inverse of the fitting matrix by Householder QR.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace hsma {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ void write_target(long long i, double x, double y, double z, double4_32a *o64, float4 *hi,
+                                             float4 *lo)
+{
+    o64[i] = make_double4_32a(x, y, z, 0.0);
+    float hx, lx, hy, ly, hz, lz;
+    split_f64(x, hx, lx);
+    split_f64(y, hy, ly);
+    split_f64(z, hz, lz);
+    hi[i] = make_float4(hx, hy, hz, 0.f);
+    lo[i] = make_float4(lx, ly, lz, 0.f);
+}
+
+// Periodic monitoring points (Sec. II.A): Fibonacci latitude grid on the
+// circumsphere, x_i for i = 1..K, then the partners x~_i = x_i - k L wrapped
+// into the central box (k = nearest integer, ties away from zero).
+__global__ void monitor_sphere_kernel(int K, double R0, double Lx, double Ly, double Lz, double4_32a *o64,
+                                      float4 *hi, float4 *lo)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    double w = (sqrt(5.0) - 1.0) * 0.5;
+    int ii = i + 1;
+    double sl = (2.0 * ii - 1.0) / K - 1.0;  // sine of the latitude
+    double cl = sqrt(fmax(0.0, 1.0 - sl * sl));
+    double az = 2.0 * kPi * ii * w;
+    double x = R0 * cl * cos(az), y = R0 * cl * sin(az), z = R0 * sl;
+    write_target(i, x, y, z, o64, hi, lo);
+    double xt = x - Lx * round(x / Lx);
+    double yt = y - Ly * round(y / Ly);
+    double zt = z - Lz * round(z / Lz);
+    write_target(K + i, xt, yt, zt, o64, hi, lo);
+}
+
+// Wall monitoring points for the grounded box: per face f (order -x, +x, -y,
+// +y, -z, +z) cnt[f] points of a 2-D golden-ratio lattice
+// ((i + 1/2)/n, frac(i w + 1/2)) over the face.
+struct FaceCounts {
+    int cnt[6];
+    int off[6];
+};
+
+__global__ void monitor_faces_kernel(FaceCounts fc, int K, double Lx, double Ly, double Lz, double4_32a *o64,
+                                     float4 *hi, float4 *lo)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    int f = 0;
+    while (f < 5 && i >= fc.off[f] + fc.cnt[f]) ++f;
+    int j = i - fc.off[f];
+    int n = fc.cnt[f];
+    double w = (sqrt(5.0) - 1.0) * 0.5;
+    double u = (j + 0.5) / n;
+    double v = fmod(j * w + 0.5, 1.0);
+    double L[3] = {Lx, Ly, Lz};
+    int a = f / 2;
+    int ua = (a == 0) ? 1 : 0;
+    int va = (a == 2) ? 1 : 2;
+    double p[3];
+    p[a] = ((f & 1) ? 0.5 : -0.5) * L[a];
+    p[ua] = (u - 0.5) * L[ua];
+    p[va] = (v - 0.5) * L[va];
+    write_target(i, p[0], p[1], p[2], o64, hi, lo);
+}
+
+// Fibonacci integration (Sec. II.B): node j = 0..F2 gives the directions
+// (theta_j, phi_j) and (theta_j, phi_j + pi) with cos(theta_j) = z_j +
+// sin(pi z_j)/pi, z_j = -1 + 2j/F2, phi_j = pi j F1 / F2, both weighted
+// (2 pi Rs^2 / F2)(1 + cos(pi z_j)).  Stored as (u_x, u_y, u_z, w).
+__global__ void quadrature_kernel(int F2, int F1, double Rs, double4_32a *dirs)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > F2) return;
+    double zj = -1.0 + 2.0 * j / F2;
+    double ct = fmin(1.0, fmax(-1.0, zj + sin(kPi * zj) / kPi));
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    // phi_j reduced exactly modulo 2 pi: j F1 mod 2 F2 in integer arithmetic
+    long long num = ((long long)j * (long long)F1) % (2LL * F2);
+    double ph = kPi * (double)num / (double)F2;
+    double w = 2.0 * kPi * Rs * Rs / F2 * (1.0 + cos(kPi * zj));
+    dirs[2 * j] = make_double4_32a(st * cos(ph), st * sin(ph), ct, w);
+    dirs[2 * j + 1] = make_double4_32a(-st * cos(ph), -st * sin(ph), ct, w);
+}
+
+// Orthonormal real solid harmonics (|x|/Rs)^n Y_nm by the Cartesian
+// recurrence: with (x, y, z) scaled by 1/Rs and r2 = x^2 + y^2 + z^2,
+//   (x + i y)^m = C_m + i S_m,
+//   Pi_m^m = (2m-1)!!,  Pi_{m+1}^m = (2m+1) z Pi_m^m,
+//   (n-m) Pi_n^m = (2n-1) z Pi_{n-1}^m - (n+m-1) r2 Pi_{n-2}^m,
+// so that r^n P_n^m(cos theta) e^{i m phi} = Pi_n^m (x + i y)^m.  Column
+// k = n^2 + n + m holds norm[k] * Pi_n^|m| * (C_m for m >= 0, S_|m| for m < 0),
+// norm[k] = sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-|m|)!/(n+|m|)!).
+// One thread per point; the recurrence runs over m outer, n inner.
+__global__ void basis_kernel(int P, double inv_rs, long long np, const double *__restrict__ pts, int stride,
+                             const double *__restrict__ norm, double *__restrict__ out, long long ld)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double x = pts[i * stride] * inv_rs, y = pts[i * stride + 1] * inv_rs, z = pts[i * stride + 2] * inv_rs;
+    double r2 = x * x + y * y + z * z;
+    double *o = out + i * ld;
+    double cm = 1.0, sm = 0.0;   // (x + i y)^m
+    double pmm = 1.0;            // Pi_m^m
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            double c2 = cm * x - sm * y;
+            sm = sm * x + cm * y;
+            cm = c2;
+            pmm *= (2.0 * m - 1.0);
+        }
+        double p2 = 0.0, p1 = pmm;  // Pi_{n-2}, Pi_{n-1}
+        for (int n = m; n <= P; ++n) {
+            double pn;
+            if (n == m)
+                pn = pmm;
+            else if (n == m + 1)
+                pn = (2.0 * m + 1.0) * z * pmm;
+            else
+                pn = ((2.0 * n - 1.0) * z * p1 - (n + m - 1.0) * r2 * p2) / (double)(n - m);
+            if (n > m) {
+                p2 = p1;
+                p1 = pn;
+            }
+            int kc = n * n + n + m;
+            o[kc] = norm[kc] * pn * cm;
+            if (m > 0) {
+                int ks = n * n + n - m;
+                o[ks] = norm[ks] * pn * sm;
+            }
+        }
+    }
+}
+
+// Fitting matrix: periodic  M_ik = B_{k+1}(x_i) - B_{k+1}(x~_i)  (column 0
+// dropped, it is identically zero); grounded M_ik = B_k(x_i).  Written both
+// column-major (for the QR) and row-major (for the refinement residual).
+__global__ void fitting_matrix_kernel(int K, int Nb, int ncols, int drop, const double *Bx, const double *Bxt,
+                                      double *Mcol, double *Mrow)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)K * ncols) return;
+    int i = (int)(t / ncols), c = (int)(t % ncols);
+    int k = c + drop;
+    double v = Bx[(long long)i * Nb + k];
+    if (Bxt) v -= Bxt[(long long)i * Nb + k];
+    Mrow[t] = v;
+    Mcol[(long long)c * K + i] = v;
+}
+
+// ---------------------------------------------------------------- QR
+// Column equilibration: scale[c] = 1/||W(:,c)||, W(:,c) *= scale[c].
+__global__ void equilibrate_kernel(double *W, int K, double *scale, int *rank_ok)
+{
+    __shared__ double red[32];
+    int c = blockIdx.x;
+    double *col = W + (long long)c * K;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s += col[i] * col[i];
+    s = block_sum(s, red);
+    double sc = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    if (s == 0.0 && threadIdx.x == 0) *rank_ok = 0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) col[i] *= sc;
+    if (threadIdx.x == 0) scale[c] = sc;
+}
+
+// Householder step j (Golub & Van Loan, Alg. 5.2.1 in spirit): block 0
+// records the reflector v = W(j:,j) - alpha e_1 (its top entry vtop, its
+// squared norm vv and R_jj = alpha); block b >= 1 applies the reflector to
+// column j + b.  Column j itself is not modified in this launch.
+__global__ void qr_step_kernel(double *W, int K, int n, int j, double *vtop, double *vv, double *diag,
+                               int *rank_ok)
+{
+    __shared__ double red[32];
+    const double *cj = W + (long long)j * K;
+    double below = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < K; i += blockDim.x) below += cj[i] * cj[i];
+    below = block_sum(below, red);
+    double a = cj[j];
+    double nrm = sqrt(below + a * a);
+    double alpha = (a > 0.0) ? -nrm : nrm;
+    double v0 = a - alpha;
+    double vvj = below + v0 * v0;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            vtop[j] = v0;
+            vv[j] = vvj;
+            diag[j] = alpha;
+            if (!(nrm > 0.0)) *rank_ok = 0;
+        }
+        return;
+    }
+    if (!(vvj > 0.0)) return;
+    int c = j + blockIdx.x;
+    if (c >= n) return;
+    double *cc = W + (long long)c * K;
+    double d = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < K; i += blockDim.x) d += cj[i] * cc[i];
+    d = block_sum(d, red);
+    d += v0 * cc[j];
+    double tau = 2.0 * d / vvj;
+    if (threadIdx.x == 0) cc[j] -= tau * v0;
+    for (int i = j + 1 + threadIdx.x; i < K; i += blockDim.x) cc[i] -= tau * cj[i];
+}
+
+// Column c of Q_1 = H_0 H_1 ... H_{n-1} [I_n; 0]: start from e_c and apply the
+// reflectors from the last to the first.  The K-vector lives in shared memory.
+__global__ void qr_form_q_kernel(const double *W, int K, int n, const double *vtop, const double *vv,
+                                 double *Q1 /* K x n column-major */)
+{
+    extern __shared__ double y[];
+    __shared__ double red[32];
+    int c = blockIdx.x;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) y[i] = (i == c) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        const double *cj = W + (long long)j * K;
+        double d = 0.0;
+        for (int i = j + 1 + threadIdx.x; i < K; i += blockDim.x) d += cj[i] * y[i];
+        d = block_sum(d, red);
+        d += vtop[j] * y[j];
+        double tau = (vv[j] > 0.0) ? 2.0 * d / vv[j] : 0.0;
+        __syncthreads();
+        if (threadIdx.x == 0) y[j] -= tau * vtop[j];
+        for (int i = j + 1 + threadIdx.x; i < K; i += blockDim.x) y[i] -= tau * cj[i];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) Q1[(long long)c * K + i] = y[i];
+}
+
+// Column c of R^{-1} by back substitution (R upper triangular: strict upper
+// part in W above the diagonal, diagonal in diag).  x lives in shared memory.
+__global__ void r_inverse_kernel(const double *W, int K, int n, const double *diag, double *Rinv /* n x n row-major */)
+{
+    extern __shared__ double x[];
+    __shared__ double red[32];
+    int c = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) x[c] = 1.0 / diag[c];
+    __syncthreads();
+    for (int i = c - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1 + threadIdx.x; k <= c; k += blockDim.x) s += W[(long long)k * K + i] * x[k];
+        s = block_sum(s, red);
+        if (threadIdx.x == 0) x[i] = -s / diag[i];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Rinv[(long long)i * n + c] = x[i];
+}
+
+// M+ = S R^{-1} Q_1^T, row-major n x K:  Mp[k][i] = scale[k] sum_c Rinv[k][c] Q1[i][c].
+__global__ void pinv_gemm_kernel(int K, int n, const double *Rinv, const double *Q1, const double *scale,
+                                 double *Mp)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * K) return;
+    int k = (int)(t / K), i = (int)(t % K);
+    double s = 0.0;
+    for (int c = k; c < n; ++c) s += Rinv[(long long)k * n + c] * Q1[(long long)c * K + i];
+    Mp[t] = scale[k] * s;
+}
+
+__global__ void cond_kernel(const double *diag, int n, double *cond)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo = INFINITY, hi = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double a = fabs(diag[j]);
+        lo = fmin(lo, a);
+        hi = fmax(hi, a);
+    }
+    *cond = (lo > 0.0) ? hi / lo : INFINITY;
+}
+
+}  // namespace
+
+int launch_monitor_sphere(int K, double R0, const double L[3], double4_32a *o64, float4 *hi, float4 *lo, cudaStream_t st)
+{
+    monitor_sphere_kernel<<<(K + 127) / 128, 128, 0, st>>>(K, R0, L[0], L[1], L[2], o64, hi, lo);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *o64, float4 *hi, float4 *lo, cudaStream_t st)
+{
+    FaceCounts fc;
+    int off = 0;
+    for (int f = 0; f < 6; ++f) {
+        fc.cnt[f] = cnt[f];
+        fc.off[f] = off;
+        off += cnt[f];
+    }
+    monitor_faces_kernel<<<(off + 127) / 128, 128, 0, st>>>(fc, off, L[0], L[1], L[2], o64, hi, lo);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st)
+{
+    quadrature_kernel<<<(F2 + 1 + 127) / 128, 128, 0, st>>>(F2, F1, Rs, dirs);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_basis(int P, double Rs, long long np, const double *pts, int stride, const double *norm, double *out,
+                 long long ld, cudaStream_t st)
+{
+    if (np <= 0) return HSMA_OK;
+    basis_kernel<<<(unsigned)((np + 127) / 128), 128, 0, st>>>(P, 1.0 / Rs, np, pts, stride, norm, out, ld);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_fitting_matrix(int K, int Nb, int ncols, int drop, const double *Bx, const double *Bxt, double *Mcol,
+                          double *Mrow, cudaStream_t st)
+{
+    long long tot = (long long)K * ncols;
+    fitting_matrix_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(K, Nb, ncols, drop, Bx, Bxt, Mcol, Mrow);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+// Pseudo-inverse of the K x n matrix held column-major in Wcol (destroyed):
+// Mp (n x K row-major) = S R^{-1} Q_1^T of the column-equilibrated matrix.
+int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond_host, int *rank_ok_host,
+                         cudaStream_t st)
+{
+    double *scale = nullptr, *vtop = nullptr, *vv = nullptr, *diag = nullptr, *Q1 = nullptr, *Rinv = nullptr,
+           *cond = nullptr;
+    int *rank_ok = nullptr;
+    size_t nd = (size_t)n;
+    HSMA_CUDA_TRY(cudaMalloc(&scale, nd * 4 * sizeof(double) + sizeof(double) + 16));
+    vtop = scale + nd;
+    vv = vtop + nd;
+    diag = vv + nd;
+    cond = diag + nd;
+    HSMA_CUDA_TRY(cudaMalloc(&rank_ok, sizeof(int)));
+    HSMA_CUDA_TRY(cudaMalloc(&Q1, (size_t)K * n * sizeof(double)));
+    HSMA_CUDA_TRY(cudaMalloc(&Rinv, (size_t)n * n * sizeof(double)));
+    int one = 1;
+    HSMA_CUDA_TRY(cudaMemcpyAsync(rank_ok, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+    equilibrate_kernel<<<n, 256, 0, st>>>(Wcol, K, scale, rank_ok);
+    HSMA_LAUNCHED();
+    for (int j = 0; j < n; ++j) {
+        qr_step_kernel<<<n - j, 256, 0, st>>>(Wcol, K, n, j, vtop, vv, diag, rank_ok);
+        HSMA_LAUNCHED();
+    }
+    size_t smq = (size_t)K * sizeof(double);
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(qr_form_q_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq));
+    qr_form_q_kernel<<<n, 256, smq, st>>>(Wcol, K, n, vtop, vv, Q1);
+    HSMA_LAUNCHED();
+    size_t smr = (size_t)n * sizeof(double);
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(r_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+    r_inverse_kernel<<<n, 128, smr, st>>>(Wcol, K, n, diag, Rinv);
+    HSMA_LAUNCHED();
+    long long tot = (long long)n * K;
+    pinv_gemm_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(K, n, Rinv, Q1, scale, Mp);
+    HSMA_LAUNCHED();
+    cond_kernel<<<1, 32, 0, st>>>(diag, n, cond);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    HSMA_CUDA_TRY(cudaMemcpyAsync(cond_host, cond, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(rank_ok_host, rank_ok, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(scale);
+    cudaFree(rank_ok);
+    cudaFree(Q1);
+    cudaFree(Rinv);
+    return HSMA_OK;
+}
+
+}  // namespace hsma

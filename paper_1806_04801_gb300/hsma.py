@@ -1,0 +1,313 @@
+"""Thin Python binding of libhsma (the C ABI in include/hsma.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (PyTorch provides device
+memory and streams); host arrays are numpy arrays.  If the library has not
+been built this module raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhsma.so")
+
+HSMA_OK = 0
+PERIODIC, GROUNDED = 0, 1
+FP64, FP32_ACC64, FP32_TC_FIT = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32_ACC64, "fp32_tc": FP32_TC_FIT}
+
+
+class HsmaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib().hsma_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: {msg} (code {code})")
+
+
+class hsma_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("dr_rel", ctypes.c_double), ("fib_F2", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class hsma_particles(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class hsma_out(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("forces", ctypes.c_void_p), ("potentials", ctypes.c_void_p),
+                ("n_inset", ctypes.c_int64), ("n_images", ctypes.c_int)]
+
+
+class hsma_plan_info_t(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_int), ("p", ctypes.c_int), ("n_basis", ctypes.c_int), ("n_cols", ctypes.c_int),
+                ("Kmon", ctypes.c_int), ("n_mon_targets", ctypes.c_int), ("F2", ctypes.c_int),
+                ("F1", ctypes.c_int), ("n_images", ctypes.c_int), ("n_shifts", ctypes.c_int),
+                ("Rs", ctypes.c_double), ("R0", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("dr", ctypes.c_double), ("cond_estimate", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+# Every exported entry point with its ctypes signature (the tests check this
+# list against include/hsma.h).
+_VP, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "hsma_opts_default": (_I, [ctypes.POINTER(hsma_opts)]),
+    "hsma_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(_D), _I, _I, _D, _I, _I, ctypes.POINTER(hsma_opts)]),
+    "hsma_plan_destroy": (None, [_VP]),
+    "hsma_plan_get_info": (_I, [_VP, ctypes.POINTER(hsma_plan_info_t)]),
+    "hsma_plan_set_stream": (_I, [_VP, _VP]),
+    "hsma_plan_set_precision": (_I, [_VP, _I]),
+    "hsma_plan_footprint": (_I, [_VP, _I64, ctypes.POINTER(ctypes.c_size_t)]),
+    "hsma_plan_get_matrix": (_I, [_VP, _I, _VP, _I64]),
+    "hsma_energy_forces": (_I, [_VP, ctypes.POINTER(hsma_particles), ctypes.POINTER(hsma_out)]),
+    "hsma_energy_forces_batched": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_particles), _VP, _VP, _VP, _VP]),
+    "hsma_coulomb_sum": (_I, [_I64, _VP, _I64, _VP, _VP, _VP, _I, _VP]),
+    "hsma_basis": (_I, [_I, _D, _I64, _VP, _VP, _VP]),
+    "hsma_strerror": (ctypes.c_char_p, [_I]),
+    "hsma_version": (ctypes.c_char_p, []),
+    "hsma_kernel_launches": (_I64, []),
+    "hsma_last_timings": (_I, [_VP, _VP, _I]),
+    "hsma_last_get": (_I64, [_VP, _I, _VP, _I64]),
+}
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhsma.so is not built ({LIB_PATH}); run __graft_entry__.build() or "
+                               "python -m paper_1806_04801_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def lib():
+    """The loaded library (ctypes.CDLL)."""
+    return _lib()
+
+
+def _check(code, where):
+    if code != HSMA_OK:
+        raise HsmaError(code, where)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr_and_dev(a):
+    if _is_torch(a):
+        if not a.is_contiguous() or a.dtype.itemsize != 8:
+            raise ValueError("tensors must be contiguous float64")
+        return a.data_ptr(), bool(a.is_cuda)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data, False
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def kernel_launches() -> int:
+    return int(_lib().hsma_kernel_launches())
+
+
+def version() -> str:
+    return _lib().hsma_version().decode()
+
+
+def strerror(code: int) -> str:
+    return _lib().hsma_strerror(int(code)).decode()
+
+
+class Plan:
+    """hsma_plan: preparation step; device-resident matrices."""
+
+    def __init__(self, box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64,
+                 dr_rel: float = 0.0, fib_F2: int = 0, stream=None, profile: bool = False, use_graphs: bool = True):
+        L = _lib()
+        o = hsma_opts()
+        _check(L.hsma_opts_default(ctypes.byref(o)), "hsma_opts_default")
+        o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+        o.dr_rel = float(dr_rel)
+        o.fib_F2 = int(fib_F2)
+        o.stream = _stream_handle(stream)
+        o.profile = 1 if profile else 0
+        o.use_graphs = 1 if use_graphs else 0
+        box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
+        h = ctypes.c_void_p()
+        _check(L.hsma_plan(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon), ctypes.byref(o)),
+               "hsma_plan")
+        self._h = h
+        self.box = tuple(float(b) for b in box)
+
+    # ------------------------------------------------------------- info
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = hsma_plan_info_t()
+        _check(_lib().hsma_plan_get_info(self._h, ctypes.byref(i)), "hsma_plan_get_info")
+        return {k: getattr(i, k) for k, _ in hsma_plan_info_t._fields_}
+
+    def set_stream(self, stream):
+        _check(_lib().hsma_plan_set_stream(self._h, _stream_handle(stream)), "hsma_plan_set_stream")
+
+    def set_precision(self, precision):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        _check(_lib().hsma_plan_set_precision(self._h, int(precision)), "hsma_plan_set_precision")
+
+    def footprint(self, n: int) -> int:
+        b = ctypes.c_size_t()
+        _check(_lib().hsma_plan_footprint(self._h, int(n), ctypes.byref(b)), "hsma_plan_footprint")
+        return int(b.value)
+
+    def get_matrix(self, which: int) -> np.ndarray:
+        info = self.info()
+        shapes = {0: (info["n_mon_targets"], 3), 1: (info["Kmon"], info["n_cols"]),
+                  2: (info["n_cols"], info["Kmon"]), 3: (2 * (info["F2"] + 1), 3), 4: (2 * (info["F2"] + 1),),
+                  5: (2 * (info["F2"] + 1), info["n_basis"])}
+        out = np.empty(shapes[which])
+        _check(_lib().hsma_plan_get_matrix(self._h, int(which), out.ctypes.data, out.size), "hsma_plan_get_matrix")
+        return out
+
+    def last_get(self, which: int, count: int) -> np.ndarray:
+        out = np.empty(count)
+        n = _lib().hsma_last_get(self._h, int(which), out.ctypes.data, count)
+        if n < 0:
+            raise HsmaError(int(n), "hsma_last_get")
+        return out[:n]
+
+    def last_timings(self) -> list:
+        ms = np.zeros(8)
+        n = _lib().hsma_last_timings(self._h, ms.ctypes.data, 8)
+        if n < 0:
+            raise HsmaError(int(n), "hsma_last_timings")
+        return list(ms[:n])
+
+    # ------------------------------------------------------------- update
+    def energy_forces(self, xyz, q, forces=True, potentials=False):
+        """hsma_energy_forces.  xyz (n, 3) and q (n,) float64, both numpy
+        (host) or both torch CUDA tensors (device).  Returns
+        (energy, forces or None, potentials or None, n_inset)."""
+        pxyz, dev = _ptr_and_dev(xyz)
+        pq, dev2 = _ptr_and_dev(q)
+        if dev != dev2:
+            raise ValueError("xyz and q must both be host or both device arrays")
+        n = int(q.shape[0])
+        if tuple(xyz.shape) != (n, 3):
+            raise ValueError("xyz must have shape (n, 3)")
+        f = p = None
+        if dev:
+            import torch
+            if forces:
+                f = torch.empty((n, 3), dtype=torch.float64, device=xyz.device)
+            if potentials:
+                p = torch.empty((n,), dtype=torch.float64, device=xyz.device)
+        else:
+            if forces:
+                f = np.empty((n, 3))
+            if potentials:
+                p = np.empty(n)
+        part = hsma_particles(n, pxyz, pq, 1 if dev else 0)
+        out = hsma_out(0.0, _ptr_and_dev(f)[0] if f is not None else None,
+                       _ptr_and_dev(p)[0] if p is not None else None, 0, 0)
+        _check(_lib().hsma_energy_forces(self._h, ctypes.byref(part), ctypes.byref(out)), "hsma_energy_forces")
+        return out.energy, f, p, out.n_inset
+
+    def energy_forces_batched(self, xyz, q, offsets, forces=True, potentials=False):
+        """hsma_energy_forces_batched over concatenated systems; offsets is a
+        sequence of nsys+1 increasing integers.  Returns (energies, forces,
+        potentials, status)."""
+        pxyz, dev = _ptr_and_dev(xyz)
+        pq, _ = _ptr_and_dev(q)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nsys = off.shape[0] - 1
+        n = int(off[-1])
+        f = p = None
+        if dev:
+            import torch
+            if forces:
+                f = torch.empty((n, 3), dtype=torch.float64, device=xyz.device)
+            if potentials:
+                p = torch.empty((n,), dtype=torch.float64, device=xyz.device)
+        else:
+            if forces:
+                f = np.empty((n, 3))
+            if potentials:
+                p = np.empty(n)
+        e = np.empty(nsys)
+        st = np.zeros(nsys, dtype=np.int32)
+        part = hsma_particles(n, pxyz, pq, 1 if dev else 0)
+        rc = _lib().hsma_energy_forces_batched(self._h, nsys, off.ctypes.data, ctypes.byref(part), e.ctypes.data,
+                                               _ptr_and_dev(f)[0] if f is not None else None,
+                                               _ptr_and_dev(p)[0] if p is not None else None, st.ctypes.data)
+        _check(rc, "hsma_energy_forces_batched")
+        return e, f, p, st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().hsma_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def coulomb_sum(src, tgt, field=True, precision=FP32_ACC64, stream=None):
+    """hsma_coulomb_sum on torch CUDA tensors: src (ns, 4) = (x, y, z, q),
+    tgt (nt, 3).  Returns (pot, field or None)."""
+    import torch
+    ps, dev = _ptr_and_dev(src)
+    pt, dev2 = _ptr_and_dev(tgt)
+    if not (dev and dev2):
+        raise ValueError("coulomb_sum takes CUDA tensors")
+    nt = tgt.shape[0]
+    pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
+    fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    _check(_lib().hsma_coulomb_sum(src.shape[0], ps, nt, pt, pot.data_ptr(),
+                                   fld.data_ptr() if fld is not None else None, int(precision),
+                                   _stream_handle(stream)), "hsma_coulomb_sum")
+    return pot, fld
+
+
+def basis(pts, p: int, Rs: float, stream=None):
+    """hsma_basis on a torch CUDA tensor of points (np, 3)."""
+    import torch
+    pp, dev = _ptr_and_dev(pts)
+    if not dev:
+        raise ValueError("basis takes a CUDA tensor")
+    out = torch.empty((pts.shape[0], (p + 1) ** 2), dtype=torch.float64, device=pts.device)
+    _check(_lib().hsma_basis(int(p), float(Rs), pts.shape[0], pp, out.data_ptr(), _stream_handle(stream)),
+           "hsma_basis")
+    return out

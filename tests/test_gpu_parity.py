@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Sizes are chosen so the oracle finishes in seconds while the GPU work still
+spans many target blocks and source tiles with ragged tails; the large
+periodic workload is checked on sampled particles at full size, in the same
+launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import TOL, assert_within, errors, rms, to_dev
+from paper_1806_04801_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "the -m gpu tests need a CUDA device"
+    from paper_1806_04801_gb300 import build
+    build.build()
+
+
+def hs():
+    from paper_1806_04801_gb300 import hsma
+    return hsma
+
+
+def oracle_run(xyz, q, w, sample=None, nthreads=8, F2=None):
+    from oracle import hsma as oh
+    F2 = F2 or oh.fib_from_points(w.Q)[0]
+    plan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    return oh.energy_forces(xyz, q, plan, nthreads=nthreads, sample=sample), plan
+
+
+PREC = ["fp64", "fp32", "fp32_tc"]
+
+
+@pytest.fixture(scope="module")
+def small_periodic():
+    xyz, q = I.small_periodic()
+    ref, oplan = oracle_run(xyz, q, I.SMALL_PERIODIC)
+    return xyz, q, ref, oplan
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_small_periodic_energy_forces(small_periodic, prec):
+    xyz, q, ref, _ = small_periodic
+    w = I.SMALL_PERIODIC
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+        dx, dq = to_dev(xyz, q)
+        U, F, pot, ns = plan.energy_forces(dx, dq, forces=True, potentials=True)
+        assert ns == ref["n_inset"]
+        e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+        assert_within(e, prec, "small periodic")
+        # intermediates: the fitted far field at the particles and the rhs.
+        # FP64: the literal dipole layer (charges +-p/dr, dr = 1e-5 Rs) cancels
+        # ~5 digits in both implementations, so Phi_out agrees to ~1e-10, not
+        # 1e-15.  FP32: b = Phi(x~) - Phi(x) cancels the monitoring potentials
+        # by a factor ~rms(Phi_mon)/rms(b), so its relative error is that factor
+        # times the ~1e-7 of the pair sums.
+        phi_out = plan.last_get(4, len(q))
+        tol = 1e-9 if prec == "fp64" else 1e-5
+        assert rms(phi_out - ref["phi_out"]) <= tol * rms(ref["phi_out"])
+        b = plan.last_get(1, w.Kmon)
+        phi_mon = plan.last_get(2, 2 * w.Kmon)
+        assert rms(phi_mon - np.concatenate([ref["phi_mon"], ref["phi_mon_partner"]])) <= \
+            (1e-13 if prec == "fp64" else 1e-6) * rms(ref["phi_mon"])
+        assert rms(b - ref["b"]) <= (1e-11 if prec == "fp64" else 1e-5) * rms(ref["b"])
+
+
+def test_host_and_device_inputs_agree(small_periodic):
+    xyz, q, ref, _ = small_periodic
+    w = I.SMALL_PERIODIC
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        U1, F1, _, _ = plan.energy_forces(np.ascontiguousarray(xyz), np.ascontiguousarray(q))
+        dx, dq = to_dev(xyz, q)
+        U2, F2, _, _ = plan.energy_forces(dx, dq)
+        assert U1 == U2
+        assert np.array_equal(F1, F2.cpu().numpy())
+        # deterministic across calls
+        U3, F3, _, _ = plan.energy_forces(dx, dq)
+        assert U3 == U2 and np.array_equal(F3.cpu().numpy(), F1)
+
+
+def test_plan_matrices_match_oracle(small_periodic):
+    import oracle
+    from oracle import hsma as oh
+    _, _, _, oplan = small_periodic
+    w = I.SMALL_PERIODIC
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as plan:
+        info = plan.info()
+        assert info["F2"] == oplan.F2 and info["F1"] == oplan.F1 and info["n_images"] == 6 * (oplan.F2 + 1)
+        mon = plan.get_matrix(0)
+        np.testing.assert_allclose(mon[:w.Kmon], oplan.x_mon, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(mon[w.Kmon:], oplan.x_mon_partner, rtol=0, atol=1e-14)
+        dirs = plan.get_matrix(3)
+        wts = plan.get_matrix(4)
+        np.testing.assert_allclose(dirs, oplan.dirs, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(wts, oplan.weights, rtol=1e-13, atol=1e-15)
+        # pseudo-inverse: M+ M = I on the GPU's own fitting matrix
+        M = plan.get_matrix(1)
+        Mp = plan.get_matrix(2)
+        np.testing.assert_allclose(Mp @ M, np.eye(M.shape[1]), atol=1e-9)
+        # its least-squares solution agrees with the oracle's solver
+        g = np.random.default_rng(0)
+        b = g.standard_normal(M.shape[0])
+        x_ref, _ = oracle.lstsq(M, b)
+        np.testing.assert_allclose(Mp @ b, x_ref, rtol=1e-8, atol=1e-10 * np.abs(x_ref).max())
+        # basis at the integration points = oracle basis up to the known column normalisation
+        Bq = plan.get_matrix(5)
+        Bo = oracle.basis(oplan.Rs * oplan.dirs, w.p, oplan.Rs)
+        scale = np.array([np.dot(Bq[:, k], Bo[:, k]) / np.dot(Bo[:, k], Bo[:, k]) for k in range(Bq.shape[1])])
+        np.testing.assert_allclose(Bq, Bo * scale, rtol=0, atol=1e-12 * np.abs(Bq).max())
+        assert np.all(scale > 0)
+
+
+def test_basis_entry_point():
+    import math
+    import oracle
+    g = np.random.default_rng(3)
+    pts = g.standard_normal((777, 3))
+    P, Rs = 12, 1.7
+    (dp,) = to_dev(pts)
+    B = hs().basis(dp, P, Rs).cpu().numpy()
+    Bo = oracle.basis(pts, P, Rs)
+    for n in range(P + 1):
+        for m in range(-n, n + 1):
+            k = n * n + n + m
+            am = abs(m)
+            c = math.sqrt((2 if m else 1) * (2 * n + 1) / (4 * math.pi) * math.factorial(n - am) / math.factorial(n + am))
+            np.testing.assert_allclose(B[:, k], c * Bo[:, k], rtol=1e-11, atol=1e-13 * (np.abs(c * Bo[:, k]).max() + 1))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("ns,nt", [(1, 1), (511, 513), (5000, 1037), (40000, 700)])
+def test_coulomb_sum_entry_point(prec, ns, nt):
+    import oracle
+    g = np.random.default_rng(ns + nt)
+    src = np.concatenate([g.random((ns, 3)) * 2 - 1, g.standard_normal((ns, 1))], axis=1)
+    tgt = g.random((nt, 3)) * 2 - 1
+    tgt[: min(nt, ns) // 3] = src[: min(nt, ns) // 3, :3]  # some targets sit on sources: skipped
+    ds, dt = to_dev(src, tgt)
+    pot, fld = hs().coulomb_sum(ds, dt, field=True, precision=prec)
+    pr, fr = oracle.coulomb(src[:, :3], src[:, 3], tgt, field=True)
+    # the oracle skips nothing by distance: recompute with zero-distance pairs removed
+    for t in range(min(nt, ns) // 3):
+        keep = np.any(src[:, :3] != tgt[t], axis=1)
+        pr[t], fr[t] = [v[0] for v in oracle.coulomb(src[keep, :3], src[keep, 3], tgt[t:t + 1], field=True)]
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert rms(pot.cpu().numpy() - pr) <= tol * max(rms(pr), 1e-30)
+    assert rms(fld.cpu().numpy() - fr) <= tol * 10 * max(rms(fr), 1e-30)
+
+
+@pytest.fixture(scope="module")
+def grounded_small():
+    w = I.Workload("grounded-small", (1.0, 1.0, 2.0), I.GROUNDED, 10, I.GROUNDED_CAVITY.R, 6000, 1500)
+    xyz, q = I.uniform_pm1(1500, w.box, seed_offset=20, margin=0.05)
+    ref, _ = oracle_run(xyz, q, w)
+    return w, xyz, q, ref
+
+
+@pytest.mark.parametrize("prec", PREC)
+def test_grounded_cavity_small(grounded_small, prec):
+    w, xyz, q, ref = grounded_small
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+        dx, dq = to_dev(xyz, q)
+        U, F, pot, ns = plan.energy_forces(dx, dq, potentials=True)
+        assert ns == ref["n_inset"]
+        e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+        assert_within(e, prec, "grounded")
+
+
+@pytest.mark.parametrize("n", [2, 3, 511, 512, 513, 4097])
+def test_ragged_sizes_fp64(n):
+    w = I.Workload("tiny", (1.0, 1.0, 1.0), I.PERIODIC, 6, 1.5, 600, 200)
+    xyz, q = I.random_neutral(n + (n % 2), w.box, seed_offset=30 + n)
+    ref, _ = oracle_run(xyz, q, w)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as plan:
+        dx, dq = to_dev(xyz, q)
+        U, F, _, ns = plan.energy_forces(dx, dq)
+        assert ns == ref["n_inset"]
+        assert_within(errors(F.cpu().numpy(), ref["forces"], U, ref["energy"]), "fp64", f"n={n}")
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        U, F, _, _ = plan.energy_forces(dx, dq)
+        assert_within(errors(F.cpu().numpy(), ref["forces"], U, ref["energy"]), "fp32", f"n={n}")
+
+
+def test_error_codes():
+    hsma = hs()
+    w = I.SMALL_PERIODIC
+    with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon) as plan:
+        xyz, q = I.small_periodic()
+        q2 = q.copy()
+        q2[0] += 0.5
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces(*to_dev(xyz, q2))
+        assert ei.value.code == -2
+        xyz2 = xyz.copy()
+        xyz2[5] = xyz2[17]
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces(*to_dev(xyz2, q))
+        assert ei.value.code == -4
+        xyz3 = xyz.copy()
+        xyz3[3, 1] = np.nan
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces(*to_dev(xyz3, q))
+        assert ei.value.code == -3
+        # the plan stays usable after errors
+        U, F, _, _ = plan.energy_forces(*to_dev(xyz, q))
+        assert np.isfinite(U)
+    g = I.GROUNDED_CAVITY
+    with hsma.Plan(g.box, g.bc, 6, g.R, 600, 200) as plan:
+        xyz, q = I.uniform_pm1(100, g.box, seed_offset=40, margin=0.05)
+        xyz[7, 2] = 2.5
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces(*to_dev(xyz, q))
+        assert ei.value.code == -3
+    with pytest.raises(hsma.HsmaError):
+        hsma.Plan((1, 1, 1), 0, 8, 0.5, 2000, 600)  # sphere inside the box
+    with pytest.raises(hsma.HsmaError):
+        hsma.Plan((1, 1, 1), 0, 8, 1.5, 2000, 10)  # fewer monitoring points than columns
+
+
+def test_batched_matches_single_and_oracle():
+    w = I.BATCH_PERIODIC
+    sizes = [600, 1000, 1500, 2048, 333 * 2]
+    systems = [I.uniform_pm1(n, w.box, seed_offset=50 + i) for i, n in enumerate(sizes)]
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    for prec in ("fp64", "fp32"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            dx, dq = to_dev(xyz, q)
+            E, F, _, st = plan.energy_forces_batched(dx, dq, off)
+            F = F.cpu().numpy()
+            assert np.all(st == 0)
+            for i, (sx, sq) in enumerate(systems):
+                U1, F1, _, _ = plan.energy_forces(*to_dev(sx, sq))
+                sl = slice(off[i], off[i + 1])
+                assert abs(E[i] - U1) <= TOL[prec]["energy"] * abs(U1)
+                assert rms(F[sl] - F1.cpu().numpy()) <= TOL[prec]["force_rms"] * rms(F1.cpu().numpy())
+                if i in (0, 3):
+                    ref, _ = oracle_run(sx, sq, w)
+                    assert_within(errors(F[sl], ref["forces"], E[i], ref["energy"]), prec, f"batched sys {i}")
+
+
+@pytest.mark.slow
+def test_large_periodic_sampled_full_size():
+    """The benchmarked workload at full size (100000 charges, p = 12): FP32 and
+    FP64 GPU results on sampled particles against the oracle, and the FP32
+    energy against the FP64 GPU energy."""
+    w = I.LARGE_PERIODIC
+    xyz, q = I.large_periodic()
+    sample = np.linspace(0, len(q) - 1, 48).astype(np.int64)
+    ref, _ = oracle_run(xyz, q, w, sample=sample, nthreads=16)
+    dx, dq = to_dev(xyz, q)
+    res = {}
+    for prec in ("fp32", "fp64"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            U, F, pot, ns = plan.energy_forces(dx, dq, potentials=True)
+            assert ns == ref["n_inset"]
+            res[prec] = (U, F.cpu().numpy(), pot.cpu().numpy())
+            e = errors(res[prec][1][sample], ref["forces"], None, None, res[prec][2][sample], ref["pot"])
+            tol = TOL[prec]
+            assert e["force_rms"] <= tol["force_rms"] and e["pot_rms"] <= tol["pot_rms"], (prec, e)
+    U32, U64 = res["fp32"][0], res["fp64"][0]
+    assert abs(U32 - U64) <= 1e-6 * abs(U64)
+    assert rms(res["fp32"][1] - res["fp64"][1]) <= 1e-5 * rms(res["fp64"][1])

@@ -195,6 +195,34 @@ int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offset
 int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tgt, double *pot,
                      double *field, int precision, void *stream);
 
+/* Size of the device array hsma_coulomb_sum_static works in (32 MiB). */
+#define HSMA_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* The sums of hsma_coulomb_sum, for callers that cannot allocate device
+ * memory while they run -- for example a host application whose own memory
+ * manager owns the whole device and forbids outside allocations after
+ * start-up, or a time-critical loop that cannot afford the device-wide
+ * synchronisation cudaFree implies.  The paper has no counterpart; this is a
+ * deployment variant of the direct sum.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: all working
+ * memory is one static device array of HSMA_STATIC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads this part of the library keeps until
+ * the process exits.  Arguments, layout and results are those of
+ * hsma_coulomb_sum.  A call must fit in the array, roughly
+ * 32 ns + 128 nt bytes (sources as two 16-byte words or one 32-byte FP64
+ * record, targets with one partial-sum chunk); a larger call returns
+ * HSMA_E_CAPACITY and does no work.  The array is shared by all calls on a
+ * device and keeps what the last call left in it (each call first clears its
+ * counters); calls whose device work overlaps -- two streams, two host
+ * threads -- race on it and give wrong results, so serialise them.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Returns once pot/field hold the results.
+ * Errors: HSMA_E_ARG, HSMA_E_CAPACITY, HSMA_E_TIMEOUT, HSMA_E_CUDA. */
+int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const double *tgt, double *pot,
+                            double *field, int precision, void *stream);
+
 /* Harmonic basis of Eq. "harmonic" at np points (device pointers; pts
  * np x 3, out np x (p+1)^2 row-major): the orthonormal real solid harmonics
  * (|x|/Rs)^n Y_nm, index k = n^2 + n + m, m > 0 the cosine and m < 0 the sine

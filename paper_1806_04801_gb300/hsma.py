@@ -67,6 +67,7 @@ SIGNATURES = {
     "hsma_energy_forces": (_I, [_VP, ctypes.POINTER(hsma_particles), ctypes.POINTER(hsma_out)]),
     "hsma_energy_forces_batched": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_particles), _VP, _VP, _VP, _VP]),
     "hsma_coulomb_sum": (_I, [_I64, _VP, _I64, _VP, _VP, _VP, _I, _VP]),
+    "hsma_coulomb_sum_static": (_I, [_I64, _VP, _I64, _VP, _VP, _VP, _I, _VP]),
     "hsma_basis": (_I, [_I, _D, _I64, _VP, _VP, _VP]),
     "hsma_strerror": (ctypes.c_char_p, [_I]),
     "hsma_version": (ctypes.c_char_p, []),
@@ -298,6 +299,26 @@ def coulomb_sum(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     _check(_lib().hsma_coulomb_sum(src.shape[0], ps, nt, pt, pot.data_ptr(),
                                    fld.data_ptr() if fld is not None else None, int(precision),
                                    _stream_handle(stream)), "hsma_coulomb_sum")
+    return pot, fld
+
+
+def coulomb_sum_static(src, tgt, field=True, precision=FP32_ACC64, stream=None):
+    """hsma_coulomb_sum_static: the same sums with no device allocation (its
+    working memory is a fixed static device array inside the library; calls
+    must not overlap on the GPU).  CUDA tensors as for coulomb_sum."""
+    import torch
+    ps, dev = _ptr_and_dev(src)
+    pt, dev2 = _ptr_and_dev(tgt)
+    if not (dev and dev2):
+        raise ValueError("coulomb_sum_static takes CUDA tensors")
+    nt = tgt.shape[0]
+    pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
+    fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    _check(_lib().hsma_coulomb_sum_static(src.shape[0], ps, nt, pt, pot.data_ptr(),
+                                          fld.data_ptr() if fld is not None else None, int(precision),
+                                          _stream_handle(stream)), "hsma_coulomb_sum_static")
     return pot, fld
 
 

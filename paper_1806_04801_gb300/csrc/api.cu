@@ -59,6 +59,8 @@ struct Workspace {
     double4_32a *src64 = nullptr;                       // in-set, FP64
     int *counts = nullptr;
     long long *ns = nullptr;
+    int *keys = nullptr, *perm = nullptr, *keys2 = nullptr, *vals2 = nullptr, *hist = nullptr;
+    float4 *boxes = nullptr;
     float4 *partials = nullptr;
     double *phi_tgt = nullptr, *e_part = nullptr;
     double *b = nullptr, *A = nullptr;
@@ -73,7 +75,8 @@ struct Workspace {
 
 struct BatchShape {
     int nsys = 0;
-    long long n_total = 0, cap_total = 0, cnt_total = 0, rec_total = 0, tgt_total = 0;
+    long long n_total = 0, cap_total = 0, cnt_total = 0, rec_total = 0, tgt_total = 0, hist_total = 0,
+              tiles_total = 0, max_tiles = 0;
     int items = 0, surf_items = 0, nblk_max = 1;
     long long max_tgt = 0;
     std::vector<SysDesc> sys;
@@ -85,6 +88,7 @@ struct hsma_plan_s {
     double L[3];
     int bc, P, Nb, ncols, K, nmon, F2, F1, ndir, nshifts;
     double Rs, R0, dr, alpha, cond;
+    double far_rel = 1.0 / 15.0;  // near/far threshold of the FP32 pair sums, in units of Rs
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
     int num_sms, ctas[3];
@@ -199,7 +203,7 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
     }
     const double items_wanted = 24.0 * slots;
     const double chunk = std::max(4.0 * tile, work / items_wanted);
-    long long part = 0, src = 0, tgt = 0, rec = 0, cnt = 0;
+    long long part = 0, src = 0, tgt = 0, rec = 0, cnt = 0, hist = 0, tiles = 0, max_tiles = 0;
     long long items = 0, surf = 0;
     int nblk_max = 1;
     long long max_tgt = 0;
@@ -211,6 +215,13 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         d.tgt_off = tgt;
         d.nblk = (int)((n[s] + kInsetBlock - 1) / kInsetBlock);
         d.cnt_off = cnt;
+        d.hist_off = hist;
+        d.tile_off = tiles;
+        // Morton grid: about 4 particles per cell, at most 32 cells per axis
+        int gb = 1;
+        while (gb < 5 && (double)(1 << (3 * gb)) * 4.0 < (double)n[s]) ++gb;
+        d.gbits = gb;
+        long long tcap = (n[s] * p->nshifts + tile - 1) / tile;
         d.ntb_part = (int)((n[s] + TB - 1) / TB);
         d.ntb = d.ntb_part + ntb_mon;
         long long maxchunks = std::max(1LL, (long long)(ns_est[s] / tile));
@@ -224,6 +235,9 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         tgt += ntgt;
         rec += (long long)d.nchunks * ntgt;
         cnt += (long long)p->nshifts * d.nblk;
+        hist += 256LL * d.nblk;
+        tiles += tcap;
+        max_tiles = std::max(max_tiles, tcap);
         items += (long long)d.ntb * d.nchunks;
         surf += (n[s] + STB - 1) / STB;
         nblk_max = std::max(nblk_max, d.nblk);
@@ -234,6 +248,9 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
     sh->tgt_total = tgt;
     sh->rec_total = rec;
     sh->cnt_total = cnt;
+    sh->hist_total = hist;
+    sh->tiles_total = tiles;
+    sh->max_tiles = max_tiles;
     sh->items = (int)items;
     sh->surf_items = (int)surf;
     sh->nblk_max = nblk_max;
@@ -259,6 +276,12 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     }
     w->counts = c.take<int>(sh.cnt_total);
     w->ns = c.take<long long>(sh.nsys);
+    w->keys = c.take<int>(sh.n_total);
+    w->perm = c.take<int>(sh.n_total);
+    w->keys2 = c.take<int>(sh.n_total);
+    w->vals2 = c.take<int>(sh.n_total);
+    w->hist = c.take<int>(sh.hist_total);
+    w->boxes = (precision == HSMA_FP64) ? nullptr : c.take<float4>(2 * sh.tiles_total);
     w->partials = c.take<float4>(2 * sh.rec_total);
     w->phi_tgt = c.take<double>(sh.tgt_total);
     w->e_part = c.take<double>(3 * sh.tgt_total);
@@ -369,6 +392,21 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     HSMA_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int) * nsys, st));
     HSMA_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
 
+    // spatial order of the particles (Morton, stable radix sort)
+    SortArgs sa;
+    sa.sys = w.sys;
+    sa.nsys = nsys;
+    sa.xyz = xyz;
+    for (int a = 0; a < 3; ++a) sa.g.L[a] = p->L[a];
+    sa.g.Rs = p->Rs;
+    sa.g.bc = p->bc;
+    sa.keys = w.keys;
+    sa.vals = w.perm;
+    sa.keys2 = w.keys2;
+    sa.vals2 = w.vals2;
+    sa.hist = w.hist;
+    if ((rc = launch_sort_particles(sa, sh.nblk_max, st))) return rc;
+
     // (a1) in-set
     InsetArgs ia;
     ia.sys = w.sys;
@@ -376,6 +414,7 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     ia.nblk_max = sh.nblk_max;
     ia.xyz = xyz;
     ia.q = q;
+    ia.perm = w.perm;
     ia.shifts = p->shifts;
     ia.n_shifts = p->nshifts;
     for (int a = 0; a < 3; ++a) ia.g.L[a] = p->L[a];
@@ -388,6 +427,7 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     ia.src64 = w.src64;
     ia.status = w.status;
     if ((rc = launch_inset(ia, st))) return rc;
+    if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, 512, w.boxes, st))) return rc;
     record(p, 1);
 
     // (a2) near-field sums at particles and monitoring targets
@@ -405,6 +445,8 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     pa.n_ext = p->nmon;
     pa.ext_field = 0;
     pa.ext_skip_zero = 0;
+    pa.boxes = w.boxes;
+    pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
     pa.next_item = w.ctrl;
     pa.status = w.status;
@@ -434,8 +476,8 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     record(p, 6);
     double *f_dst = on_dev ? forces : (forces ? w.forces : nullptr);
     double *p_dst = on_dev ? pot : (pot ? w.pot : nullptr);
-    if ((rc = launch_finalize(w.sys, nsys, q, w.phi_tgt, w.e_part, w.phi_out, w.e_out, f_dst, p_dst, w.energy,
-                              w.status, st)))
+    if ((rc = launch_finalize(w.sys, nsys, w.perm, q, w.phi_tgt, w.e_part, w.phi_out, w.e_out, f_dst, p_dst,
+                              w.energy, w.status, st)))
         return rc;
     record(p, 7);
     HSMA_CUDA_TRY(cudaMemcpyAsync(h_energy, w.energy, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
@@ -834,6 +876,15 @@ int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count
     }
     if (nd > count) return HSMA_E_ARG;
     HSMA_CUDA_TRY(cudaStreamSynchronize(pl->stream));
+    if (which == 3 || which == 4) {
+        // particle values are held in spatial order; return them in caller order
+        std::vector<double> v(nd);
+        std::vector<int> perm(nd);
+        HSMA_CUDA_TRY(cudaMemcpy(v.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost));
+        HSMA_CUDA_TRY(cudaMemcpy(perm.data(), pl->ws.perm + sd.part_off, nd * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nd; ++i) host_out[perm[i]] = v[i];
+        return nd;
+    }
     HSMA_CUDA_TRY(cudaMemcpy(host_out, src, nd * sizeof(double), cudaMemcpyDeviceToHost));
     return nd;
 }

@@ -45,6 +45,10 @@ struct SysDesc {
     long long tgt_off;      // first target slot: n particles then n_mon monitors
     long long partial_off;  // first partial record: nchunks * (n + n_mon)
     long long cnt_off;      // first in-set block count: n_shifts * nblk
+    long long hist_off;     // first radix-sort histogram entry: 256 * nblk
+    long long tile_off;     // first tile bounding box: ceil(n * n_shifts / tile)
+    int gbits;              // Morton grid of 2^gbits cells per axis
+    int pad0;
     int nchunks;            // source chunks of the near-field sums
     int ntb;                // target blocks (particles, then monitors)
     int ntb_part;           // target blocks holding particles
@@ -189,6 +193,20 @@ int launch_fitting_matrix(int K, int Nb, int ncols, int drop, const double *Bx, 
 int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond, int *rank_ok,
                          cudaStream_t st);
 
+// sort.cu
+struct SortArgs {
+    const SysDesc *sys;
+    int nsys;
+    const double *xyz;
+    Geometry g;
+    int *keys, *vals;       // in: unused; out: sorted keys and the permutation
+    int *keys2, *vals2;     // ping-pong buffers
+    int *hist;
+};
+int launch_sort_particles(const SortArgs &a, int nblk_max, cudaStream_t st);
+int launch_tile_boxes(const SysDesc *sys, int nsys, long long max_tiles, const long long *ns, const float4 *src_hi,
+                      int tile, float4 *boxes, cudaStream_t st);
+
 // inset.cu
 struct InsetArgs {
     const SysDesc *sys;
@@ -196,6 +214,7 @@ struct InsetArgs {
     int nblk_max;
     const double *xyz;
     const double *q;
+    const int *perm;        // sorted position -> particle index within its system
     const int4 *shifts;
     int n_shifts;
     Geometry g;
@@ -223,6 +242,8 @@ struct PairArgs {
     int n_ext;
     int ext_field;          // external targets also need the field
     int ext_skip_zero;      // skip pairs at distance exactly zero for external targets
+    const float4 *boxes = nullptr;  // FP32 form: box of every source tile (lo, hi), or null
+    float far2 = 0.f;               // tiles at least sqrt(far2) from the target block skip the low words
     float4 *partials;       // 2 x float4 (FP32) or 1 x double4_32a (FP64) per record
     int *next_item;
     int *status;
@@ -242,9 +263,9 @@ int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const lo
                          const float4 *src_lo, const double4_32a *src64, int ndir, const double4_32a *dirs,
                          const double2 *img, double Rs, double dr, int precision, double *phi_out,
                          double *e_out, cudaStream_t st);
-int launch_finalize(const SysDesc *sys, int nsys, const double *q, const double *phi_tgt, const double *e_part,
-                    const double *phi_out, const double *e_out, double *forces, double *pot, double *energy,
-                    int *status, cudaStream_t st);
+int launch_finalize(const SysDesc *sys, int nsys, const int *perm, const double *q, const double *phi_tgt,
+                    const double *e_part, const double *phi_out, const double *e_out, double *forces, double *pot,
+                    double *energy, int *status, cudaStream_t st);
 
 // tc_fit.cu
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,

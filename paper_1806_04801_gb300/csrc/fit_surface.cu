@@ -268,10 +268,12 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
 }
 
 // Per system: forces, potentials and U = 1/2 sum q_i phi_i (fixed order).
-__global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, const double *q, const double *phi_tgt,
-                                                        const double *e_part, const double *phi_out,
-                                                        const double *e_out, double *forces, double *pot,
-                                                        double *energy, int *status)
+// Target i of a system is its i-th particle in spatial order; perm maps it
+// back to the caller's index.
+__global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, const int *perm, const double *q,
+                                                        const double *phi_tgt, const double *e_part,
+                                                        const double *phi_out, const double *e_out, double *forces,
+                                                        double *pot, double *energy, int *status)
 {
     __shared__ double red[32];
     const int s = blockIdx.x;
@@ -279,12 +281,13 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, cons
     double u = 0.0;
     bool bad = false;
     for (long long i = threadIdx.x; i < sd.n; i += blockDim.x) {
-        long long t = sd.tgt_off + i, o = sd.part_off + i;
+        long long t = sd.tgt_off + i, so = sd.part_off + i;
+        long long o = sd.part_off + perm[so];
         double qi = q[o];
-        double ph = phi_tgt[t] + phi_out[o];
-        double ex = e_part[3 * t] + e_out[3 * o];
-        double ey = e_part[3 * t + 1] + e_out[3 * o + 1];
-        double ez = e_part[3 * t + 2] + e_out[3 * o + 2];
+        double ph = phi_tgt[t] + phi_out[so];
+        double ex = e_part[3 * t] + e_out[3 * so];
+        double ey = e_part[3 * t + 1] + e_out[3 * so + 1];
+        double ez = e_part[3 * t + 2] + e_out[3 * so + 2];
         if (!isfinite(ph) || !isfinite(ex) || !isfinite(ey) || !isfinite(ez)) bad = true;
         if (forces) {
             forces[3 * o] = qi * ex;
@@ -344,11 +347,12 @@ int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const lo
     return HSMA_OK;
 }
 
-int launch_finalize(const SysDesc *sys, int nsys, const double *q, const double *phi_tgt, const double *e_part,
-                    const double *phi_out, const double *e_out, double *forces, double *pot, double *energy,
-                    int *status, cudaStream_t st)
+int launch_finalize(const SysDesc *sys, int nsys, const int *perm, const double *q, const double *phi_tgt,
+                    const double *e_part, const double *phi_out, const double *e_out, double *forces, double *pot,
+                    double *energy, int *status, cudaStream_t st)
 {
-    finalize_kernel<<<nsys, 1024, 0, st>>>(sys, q, phi_tgt, e_part, phi_out, e_out, forces, pot, energy, status);
+    finalize_kernel<<<nsys, 1024, 0, st>>>(sys, perm, q, phi_tgt, e_part, phi_out, e_out, forces, pot, energy,
+                                           status);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

@@ -4,8 +4,9 @@
 // ((-1)^k ∘ r_j + k∘L with charge (-1)^{|k|} q_j).
 //
 // Three kernels give a deterministic compacted order -- shift k = 0 first (so
-// in-set slot i of a system is its particle i), then the other shifts in the
-// order of the shift table, each over j:
+// in-set slot i of a system is its i-th particle in spatial order, perm[i]),
+// then the other shifts in the order of the shift table, each over the
+// particles in spatial order:
 //   count   : per (system, shift, block of particles) the number of hits;
 //   scan    : per system, exclusive prefix over (shift, block) + totals, and
 //             the neutrality check of periodic systems;
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
     long long j = (long long)blk * kInsetThreads + threadIdx.x;
     int hit = 0;
     if (j < sd.n) {
-        Centred c = load_centred(a.xyz, a.q, sd.part_off + j, a.g);
+        Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
         if (sh == 0 && !c.ok) atomicOr(&a.status[sys_i], ST_OUT_OF_BOX);
         double x, y, z, q;
         hit = image_of(c, a.shifts[sh], a.g, x, y, z, q) ? 1 : 0;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_scatter_kernel(InsetArgs 
     bool hit = false;
     double x = 0, y = 0, z = 0, q = 0;
     if (j < sd.n) {
-        Centred c = load_centred(a.xyz, a.q, sd.part_off + j, a.g);
+        Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
         hit = image_of(c, a.shifts[sh], a.g, x, y, z, q);
     }
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -61,7 +61,12 @@ __device__ __forceinline__ Item decode_item(const PairArgs &a, int item)
 // ------------------------------------------------------------ FP32 tiles
 // SKIP: 0 = no exclusion; 1 = skip the target's own slot (self_rel[t] = own
 // slot - tile start); 2 = skip pairs at distance exactly zero.
-template <bool FIELD, int SKIP>
+// SPLIT: use the low words of both positions in the difference.  A tile whose
+// box is at least `far` away from the target block's box uses the high words
+// only: their rounding (<= 2^-24 |x|) then changes each distance by a relative
+// ~1e-6 or less, while the closest pairs -- where an absolute error of
+// ~1e-7 would matter -- always take the split form.
+template <bool FIELD, int SKIP, bool SPLIT>
 __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int cnt_pad,
                                        const float (&th)[kT32][3], const float (&tl)[kT32][3],
                                        const int (&self_rel)[kT32], float2 (&phi)[kT32], float2 (&g)[kT32][3])
@@ -76,12 +81,19 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
 #pragma unroll 4
         for (int s = 0; s < kFold; ++s) {
             const float4 h = sh[s0 + s];
-            const float4 l = sl[s0 + s];
+            const float4 l = SPLIT ? sl[s0 + s] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int t = 0; t < kT32; ++t) {
-                float dx = (h.x - th[t][0]) + (l.x - tl[t][0]);
-                float dy = (h.y - th[t][1]) + (l.y - tl[t][1]);
-                float dz = (h.z - th[t][2]) + (l.z - tl[t][2]);
+                float dx, dy, dz;
+                if (SPLIT) {
+                    dx = (h.x - th[t][0]) + (l.x - tl[t][0]);
+                    dy = (h.y - th[t][1]) + (l.y - tl[t][1]);
+                    dz = (h.z - th[t][2]) + (l.z - tl[t][2]);
+                } else {
+                    dx = h.x - th[t][0];
+                    dy = h.y - th[t][1];
+                    dz = h.z - th[t][2];
+                }
                 float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                 float ri = rsqrt_sfu(r2);
                 if (SKIP == 1) ri = (s0 + s == self_rel[t]) ? 0.f : ri;
@@ -174,6 +186,14 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
             g[t][0] = g[t][1] = g[t][2] = make_float2(0.f, 0.f);
         }
 
+        // box of this block's targets (= in-set tile `tb`, its particles), for
+        // the near/far decision per source tile
+        const bool use_boxes = part && a.boxes != nullptr;
+        float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
+        if (use_boxes) {
+            blo = a.boxes[2 * (sd.tile_off + it.tb)];
+            bhi = a.boxes[2 * (sd.tile_off + it.tb) + 1];
+        }
         const float4 *gh = a.src_hi + sd.src_off;
         const float4 *gl = a.src_lo + sd.src_off;
         const int ntile = t1 - t0;
@@ -214,18 +234,29 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
             int self_rel[kT32];
 #pragma unroll
             for (int t = 0; t < kT32; ++t) self_rel[t] = (int)(tidx[t] - s0);
+            bool far = false;
+            if (use_boxes && skip == 0) {
+                const float4 slo = a.boxes[2 * (sd.tile_off + t0 + k)];
+                const float4 shi = a.boxes[2 * (sd.tile_off + t0 + k) + 1];
+                float gx = fmaxf(0.f, fmaxf(slo.x - bhi.x, blo.x - shi.x));
+                float gy = fmaxf(0.f, fmaxf(slo.y - bhi.y, blo.y - shi.y));
+                float gz = fmaxf(0.f, fmaxf(slo.z - bhi.z, blo.z - shi.z));
+                far = gx * gx + gy * gy + gz * gz >= a.far2;
+            }
             if (field) {
-                if (skip == 1)
-                    tile32<true, 1>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                if (far)
+                    tile32<true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                else if (skip == 1)
+                    tile32<true, 1, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 2)
-                    tile32<true, 2>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<true, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<true, 0>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             } else {
                 if (skip == 2)
-                    tile32<false, 2>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<false, 0>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             }
             __syncthreads();
             if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);

@@ -48,7 +48,136 @@ def parse():
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
+    ap.add_argument("--workload", default="periodic", choices=["periodic", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests in the Poisson trace")
     return ap.parse_args()
+
+
+# ------------------------------------------------------- batched workload
+def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_systems: int = 24):
+    """256 periodic boxes of log-uniform size in one batched update step
+    (persistent launch over all systems, CUDA graph), against the plain
+    one-system-per-launch FP64 path."""
+    import torch
+    from paper_1806_04801_gb300 import inputs as I
+    systems = I.batch_periodic()
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    dx = torch.as_tensor(xyz).cuda()
+    dq = torch.as_tensor(q).cuda()
+    for _ in range(warmup):
+        plan_fp32.energy_forces_batched(dx, dq, off)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        E32, F32, _, st = plan_fp32.energy_forces_batched(dx, dq, off)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    # the plain paths: one system per call (FP64, and FP32 for reference), on
+    # a sample of systems
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(systems), size=min(fp64_systems, len(systems)), replace=False))
+    t64 = t32 = 0.0
+    rel, rel_raw = [], []
+    sizes = np.diff(off)
+
+    def one(plan, sx, sq):
+        plan.energy_forces(sx, sq)  # warm (plan workspace, graph)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        U, _, _, _ = plan.energy_forces(sx, sq)
+        e1.record()
+        e1.synchronize()
+        return U, e0.elapsed_time(e1)
+    for i in pick:
+        sx = torch.as_tensor(systems[i][0]).cuda()
+        sq = torch.as_tensor(systems[i][1]).cuda()
+        U64, dt = one(plan_fp64, sx, sq)
+        t64 += dt
+        t32 += one(plan_fp32, sx, sq)[1]
+        floor = 0.5 * 2.837297479 * float(np.sum(systems[i][1] ** 2))
+        rel.append(abs(E32[i] - U64) / max(abs(U64), floor))
+        rel_raw.append(abs(E32[i] - U64) / abs(U64))
+    # scale the sampled FP64 time to all systems by their share of pair work (~ N^2)
+    w_all = float(np.sum(sizes.astype(np.float64) ** 2 + 3000.0 * sizes))
+    w_pick = float(np.sum(sizes[pick].astype(np.float64) ** 2 + 3000.0 * sizes[pick]))
+    t64_all = t64 * w_all / w_pick
+    t32_all = t32 * w_all / w_pick
+    return {"workload": "batched-256-periodic-p10 (N log-uniform in [500, 50000], +-1)",
+            "systems": len(systems), "particles": int(off[-1]), "ms_per_batch": ms,
+            "systems_per_s": len(systems) / (ms / 1000.0),
+            "fp64_one_system_per_launch_systems_per_s": len(systems) / (t64_all / 1000.0),
+            "fp32_one_system_per_launch_systems_per_s": len(systems) / (t32_all / 1000.0),
+            "sampled_systems_for_single_paths": int(len(pick)),
+            "speedup_vs_fp64_single": t64_all / ms,
+            "max_rel_energy_err_vs_fp64": float(max(rel)),
+            "max_rel_energy_err_vs_fp64_unfloored": float(max(rel_raw)),
+            "energy_err_note": "denominator max(|U|, 1/2 |xi| sum q^2 / L), xi = -2.837297 (self-image scale)",
+            "precision": "fp32 pair sums, fp64 fit, CUDA graph"}
+
+
+# ------------------------------------------------------- serving workload
+def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, lanes: int = 2, max_batch: int = 32):
+    """Poisson stream of periodic boxes with N log-uniform in [1000, 200000]:
+    requests are submitted at their arrival times to the continuous-batching
+    server; latency is submit -> result."""
+    import threading
+    from paper_1806_04801_gb300 import hsma
+    from paper_1806_04801_gb300 import inputs as I
+    w = I.SERVING_PERIODIC
+
+    def replay(rate, count, seed):
+        t_arr, sizes = I.poisson_trace(count, rate_hz=rate, seed_offset=4 + seed)
+        reqs = [I.uniform_pm1(int(n), w.box, seed_offset=5000 + seed * 1000 + i) for i, n in enumerate(sizes)]
+        with hsma.Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=lanes,
+                         max_batch=max_batch) as srv:
+            # warm the lanes (plans, workspaces)
+            for _ in range(lanes):
+                tk = srv.submit(*reqs[0])
+                srv.result(tk, n=len(reqs[0][1]), forces=False)
+            tickets = [None] * count
+            t0 = time.perf_counter()
+
+            def feeder():
+                for i in range(count):
+                    delay = t0 + t_arr[i] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    tickets[i] = srv.submit(*reqs[i])
+            th = threading.Thread(target=feeder)
+            th.start()
+            lat, batch = [], []
+            th.join()
+            for i in range(count):
+                code, e, _, info = srv.result(tickets[i], n=len(reqs[i][1]), forces=False)
+                if code == 0:
+                    lat.append(info["latency_ms"])
+                    batch.append(info["batch_size"])
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        lat = np.array(lat)
+        return {"rate_hz": rate, "requests": count, "completed": int(len(lat)),
+                "systems_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(batch)),
+                "wall_s": wall, "hbm_budget_bytes": int(st["hbm_budget_bytes"])}
+
+    main = replay(rate_hz, n_requests, 0)
+    out = {"workload": "serving-periodic-p10 (Poisson arrivals, N log-uniform in [1000, 200000], +-1)",
+           "lanes": lanes, "max_batch": max_batch, "offered": main}
+    if sweep:
+        cap = main["systems_per_s"]
+        out["sweep"] = [replay(f * cap, max(20, int(n_requests * 0.3)), k + 1)
+                        for k, f in enumerate((0.25, 0.5, 0.9))]
+        out["capacity_systems_per_s"] = cap
+    return out
 
 
 def dist_env():
@@ -182,6 +311,31 @@ def main():
     from paper_1806_04801_gb300 import hsma
     from paper_1806_04801_gb300 import inputs as I
 
+    if args.workload != "periodic":
+        # one of the other workloads on its own (rank 0, one GPU)
+        if rank == 0:
+            if args.workload == "batched":
+                wb = I.BATCH_PERIODIC
+                fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+                with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=args.precision) as pb32, \
+                        hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
+                    r = run_batched(pb32, pb64, args.steps, args.warmup, fl)
+                line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,
+                        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
+                        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                        "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
+            else:
+                r = run_serving(args.requests)
+                line = {"metric": METRIC, "value": r["offered"]["systems_per_s"], "unit": "systems/s",
+                        "n_gpus": 1, "steps": args.requests, "warmup": 0, "higher_is_better": True,
+                        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                        "latency_ms": {"p50": r["offered"]["p50_ms"], "p99": r["offered"]["p99_ms"]},
+                        "config": {"workload": r["workload"]}, "detail": r}
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
     w = I.LARGE_PERIODIC
     xyz, q = I.uniform_gauss(args.n, w.box, seed_offset=1 + 1000 * rank) if rank else I.large_periodic(args.n)
     dev = torch.device("cuda", local)
@@ -270,6 +424,14 @@ def main():
                     "rms_force_err_rel": float(dF.pow(2).mean().sqrt() / F64.pow(2).mean().sqrt()),
                     "energy": Uc, "energy_fp64": U64}
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        wb = I.BATCH_PERIODIC
+        with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp32") as pb32, \
+                hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
+            extras = {"batched": run_batched(pb32, pb64, max(3, min(args.steps, 5)), 2, flush)}
+        extras["serving"] = run_serving(args.requests)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         r = cpu_oracle_rate(xyz, q, w)
@@ -308,6 +470,7 @@ def main():
         "phases_ms": dict(zip(["inset", "near_field", "chunk_reduce", "fit", "surface_charges", "surface_pairs",
                                "finalize", "total"], plan.last_timings())),
         "accuracy": accuracy,
+        "workloads": extras,
         "cpu_baseline": cpu,
         "wall_s_timed_region": wall,
     }

@@ -183,6 +183,64 @@ int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offset
                                const hsma_particles *all, double *energies, double *forces,
                                double *potentials, int *status);
 
+/* --------------------------------------------------------------- serving */
+/* A request loop with continuous batching (a deployment layer over the
+ * update step; the paper has no serving component).  The server keeps
+ * `lanes` plans with the given parameters resident (matrices and
+ * pseudo-inverse on the device), each with its own stream and workspace.  A
+ * free lane takes the oldest waiting requests -- at most max_batch systems and
+ * at most hbm_budget_bytes of device work in flight over all lanes, by
+ * hsma_plan_footprint -- and runs them as one batched update step.  Requests
+ * that arrive while other lanes are busy are admitted by the next free lane,
+ * so their device work overlaps.  A request larger than the whole budget
+ * fails with HSMA_E_CAPACITY.  Thread-safe: submit and result may be called
+ * from any host thread. */
+typedef struct hsma_server_s *hsma_server_t;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device bytes of work in flight; 0 = half the free memory */
+    int max_batch;            /* systems per batched pass (default 64)                    */
+    int lanes;                /* concurrent batched passes, 1..16 (default 2)            */
+    int precision;            /* hsma_precision of served requests (default 1)           */
+} hsma_server_opts;
+
+typedef struct {
+    int64_t n;                /* particles of the request                                */
+    double latency_ms;        /* submit -> result ready                                  */
+    double queue_ms;          /* submit -> its batch started                             */
+    int batch_size;           /* systems in the batched pass that served it              */
+    int status;               /* its code                                                */
+} hsma_request_info;
+
+typedef struct {
+    int64_t completed, failed, queued, batches;
+    double mean_batch;        /* systems per batched pass                                */
+    double elapsed_s;         /* first submit -> last completion                         */
+    size_t hbm_held_bytes, hbm_budget_bytes;
+} hsma_server_stats_t;
+
+int hsma_server_opts_default(hsma_server_opts *opts);
+
+/* Plan parameters as in hsma_plan.  Errors as hsma_plan. */
+int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, double R, int Q, int Kmon,
+                       const hsma_server_opts *opts);
+
+/* Queue one configuration (host arrays, copied before return: xyz n x 3 in
+ * the box frame, q n).  *ticket identifies it. */
+int hsma_server_submit(hsma_server_t srv, int64_t n, const double *xyz, const double *q, int64_t *ticket);
+
+/* Result of a ticket: with wait = 0 returns HSMA_E_AGAIN while it is not
+ * ready; otherwise blocks.  energy, forces (host n x 3) and info may be NULL.
+ * Returns the request's code; a ticket can be collected once
+ * (HSMA_E_NOT_FOUND afterwards). */
+int hsma_server_result(hsma_server_t srv, int64_t ticket, int wait, double *energy, double *forces,
+                       hsma_request_info *info);
+
+int hsma_server_stats(hsma_server_t srv, hsma_server_stats_t *stats);
+
+/* Finishes queued requests, then frees everything. */
+void hsma_server_destroy(hsma_server_t srv);
+
 /* ------------------------------------------------------- direct sums */
 /* Coulomb sums of Sec. II.A (Phi_in) on their own:
  *   pot[t]   = sum_s q_s / |x_t - y_s|

@@ -115,6 +115,12 @@ struct hsma_plan_s {
     bool events_ready = false;
     double last_ms[8] = {};
     bool have_timings = false;
+    // CUDA graph of the update step for the last batch shape
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<long long> graph_key;
+    long long graph_kernels = 0;
+    cudaStream_t priv_stream = nullptr;
+    cudaEvent_t order_ev = nullptr;
 };
 
 namespace {
@@ -340,63 +346,29 @@ std::vector<double> norm_table(int P)
     return v;
 }
 
-void record(hsma_plan_s *p, int i)
+void record(hsma_plan_s *p, cudaStream_t st, int i)
 {
-    if (p->profile && p->events_ready) cudaEventRecord(p->ev[i], p->stream);
+    if (p->profile && p->events_ready) cudaEventRecord(p->ev[i], st);
 }
 
-// The update step for a batch of systems sharing the plan.
-int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_particles *all, double *energies,
-               double *forces, double *pot, int *status_out, hsma_out *single)
+// Every kernel of the update step, enqueued on `st`.  Reads its inputs from
+// the workspace staging buffers and writes forces/potentials to the staging
+// outputs, so the same sequence can be captured once into a CUDA graph and
+// replayed for every call with the same batch shape.
+int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int prec, bool want_f, bool want_p,
+                   cudaStream_t st)
 {
-    if (!p || nsys < 1 || !offsets || !all || !all->xyz || !all->q) return HSMA_E_ARG;
-    if (offsets[0] != 0) return HSMA_E_ARG;
-    if (((uintptr_t)all->xyz | (uintptr_t)all->q | (uintptr_t)forces | (uintptr_t)pot) & 7) return HSMA_E_ARG;
-    std::vector<long long> n(nsys);
-    for (int s = 0; s < nsys; ++s) {
-        n[s] = offsets[s + 1] - offsets[s];
-        if (n[s] < 1) return HSMA_E_ARG;
-    }
-    const int prec = p->precision;
-    const bool on_dev = all->on_device != 0;
-    BatchShape sh;
-    shape_batch(p, nsys, n.data(), prec, &sh);
-    if (sh.items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
-    Workspace w;
-    size_t need = carve_workspace(p, sh, prec, !on_dev, !on_dev, nullptr, &w);
-    int rc = ensure_workspace(p, need);
-    if (rc) return rc;
-    carve_workspace(p, sh, prec, !on_dev, !on_dev, p->ws_mem, &w);
-    p->ws = w;
-    const size_t sys_bytes = align_up(sizeof(SysDesc) * nsys, 64);
-    const size_t pin_bytes = sys_bytes + align_up(sizeof(double) * nsys, 64) + align_up(sizeof(long long) * nsys, 64) +
-                             align_up(sizeof(int) * nsys, 64);
-    rc = ensure_pinned(p, pin_bytes);
-    if (rc) return rc;
-    SysDesc *hsys = (SysDesc *)p->hpin;
-    double *h_energy = (double *)((char *)p->hpin + sys_bytes);
-    long long *h_ns = (long long *)((char *)h_energy + align_up(sizeof(double) * nsys, 64));
-    int *h_status = (int *)((char *)h_ns + align_up(sizeof(long long) * nsys, 64));
-    memcpy(hsys, sh.sys.data(), sizeof(SysDesc) * nsys);
-    cudaStream_t st = p->stream;
-
-    record(p, 0);
-    HSMA_CUDA_TRY(cudaMemcpyAsync(w.sys, hsys, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, st));
-    const double *xyz = all->xyz, *q = all->q;
-    if (!on_dev) {
-        HSMA_CUDA_TRY(cudaMemcpyAsync(w.xyz, all->xyz, sizeof(double) * 3 * sh.n_total, cudaMemcpyHostToDevice, st));
-        HSMA_CUDA_TRY(cudaMemcpyAsync(w.q, all->q, sizeof(double) * sh.n_total, cudaMemcpyHostToDevice, st));
-        xyz = w.xyz;
-        q = w.q;
-    }
+    const int nsys = sh.nsys;
+    int rc = HSMA_OK;
     HSMA_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int) * nsys, st));
     HSMA_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
+    record(p, st, 0);
 
     // spatial order of the particles (Morton, stable radix sort)
     SortArgs sa;
     sa.sys = w.sys;
     sa.nsys = nsys;
-    sa.xyz = xyz;
+    sa.xyz = w.xyz;
     for (int a = 0; a < 3; ++a) sa.g.L[a] = p->L[a];
     sa.g.Rs = p->Rs;
     sa.g.bc = p->bc;
@@ -412,8 +384,8 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     ia.sys = w.sys;
     ia.nsys = nsys;
     ia.nblk_max = sh.nblk_max;
-    ia.xyz = xyz;
-    ia.q = q;
+    ia.xyz = w.xyz;
+    ia.q = w.q;
     ia.perm = w.perm;
     ia.shifts = p->shifts;
     ia.n_shifts = p->nshifts;
@@ -428,7 +400,7 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     ia.status = w.status;
     if ((rc = launch_inset(ia, st))) return rc;
     if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, 512, w.boxes, st))) return rc;
-    record(p, 1);
+    record(p, st, 1);
 
     // (a2) near-field sums at particles and monitoring targets
     PairArgs pa;
@@ -453,10 +425,10 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     const int ctas = p->ctas[prec == HSMA_FP64 ? 0 : 1];
     const int grid = std::max(1, std::min(sh.items, p->num_sms * ctas));
     if ((rc = launch_pair(pa, prec, grid, st))) return rc;
-    record(p, 2);
+    record(p, st, 2);
     if ((rc = launch_partial_reduce(w.sys, nsys, sh.max_tgt, p->nmon, w.partials, prec, w.phi_tgt, w.e_part, st)))
         return rc;
-    record(p, 3);
+    record(p, st, 3);
 
     // (c) fit
     if (prec == HSMA_FP32_TC_FIT)
@@ -465,28 +437,126 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     else
         rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, w.b, w.A, st);
     if (rc) return rc;
-    record(p, 4);
+    record(p, st, 4);
 
     // (d) surface images and their sums at the particles
     if ((rc = launch_surface_charges(nsys, p->ndir, p->Nb, p->Bq, p->dirs, w.A, p->Rs, w.img, st))) return rc;
-    record(p, 5);
+    record(p, st, 5);
     if ((rc = launch_surface_pairs(w.sys, nsys, sh.surf_items, w.ns, w.src_hi, w.src_lo, w.src64, p->ndir, p->dirs,
                                    w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st)))
         return rc;
-    record(p, 6);
-    double *f_dst = on_dev ? forces : (forces ? w.forces : nullptr);
-    double *p_dst = on_dev ? pot : (pot ? w.pot : nullptr);
-    if ((rc = launch_finalize(w.sys, nsys, w.perm, q, w.phi_tgt, w.e_part, w.phi_out, w.e_out, f_dst, p_dst,
-                              w.energy, w.status, st)))
+    record(p, st, 6);
+    if ((rc = launch_finalize(w.sys, nsys, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
+                              want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, w.energy, w.status, st)))
         return rc;
-    record(p, 7);
+    record(p, st, 7);
+    return HSMA_OK;
+}
+
+// The stream device work runs on: the plan's stream, or -- for the legacy
+// default stream, which cannot be captured -- a private stream ordered after
+// the caller's earlier work by an event.
+int work_stream(hsma_plan_s *p, cudaStream_t *out)
+{
+    if (p->stream) {
+        *out = p->stream;
+        return HSMA_OK;
+    }
+    if (!p->priv_stream) {
+        HSMA_CUDA_TRY(cudaStreamCreateWithFlags(&p->priv_stream, cudaStreamNonBlocking));
+        HSMA_CUDA_TRY(cudaEventCreateWithFlags(&p->order_ev, cudaEventDisableTiming));
+    }
+    HSMA_CUDA_TRY(cudaEventRecord(p->order_ev, (cudaStream_t)0));
+    HSMA_CUDA_TRY(cudaStreamWaitEvent(p->priv_stream, p->order_ev, 0));
+    *out = p->priv_stream;
+    return HSMA_OK;
+}
+
+// The update step for a batch of systems sharing the plan.
+int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_particles *all, double *energies,
+               double *forces, double *pot, int *status_out, hsma_out *single)
+{
+    if (!p || nsys < 1 || !offsets || !all || !all->xyz || !all->q) return HSMA_E_ARG;
+    if (offsets[0] != 0) return HSMA_E_ARG;
+    if (((uintptr_t)all->xyz | (uintptr_t)all->q | (uintptr_t)forces | (uintptr_t)pot) & 7) return HSMA_E_ARG;
+    std::vector<long long> n(nsys);
+    for (int s = 0; s < nsys; ++s) {
+        n[s] = offsets[s + 1] - offsets[s];
+        if (n[s] < 1) return HSMA_E_ARG;
+    }
+    const int prec = p->precision;
+    const bool on_dev = all->on_device != 0;
+    BatchShape sh;
+    shape_batch(p, nsys, n.data(), prec, &sh);
+    if (sh.items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
+    Workspace w;
+    size_t need = carve_workspace(p, sh, prec, true, true, nullptr, &w);
+    int rc = ensure_workspace(p, need);
+    if (rc) return rc;
+    carve_workspace(p, sh, prec, true, true, p->ws_mem, &w);
+    p->ws = w;
+    const size_t sys_bytes = align_up(sizeof(SysDesc) * nsys, 64);
+    const size_t pin_bytes = sys_bytes + align_up(sizeof(double) * nsys, 64) + align_up(sizeof(long long) * nsys, 64) +
+                             align_up(sizeof(int) * nsys, 64);
+    rc = ensure_pinned(p, pin_bytes);
+    if (rc) return rc;
+    SysDesc *hsys = (SysDesc *)p->hpin;
+    double *h_energy = (double *)((char *)p->hpin + sys_bytes);
+    long long *h_ns = (long long *)((char *)h_energy + align_up(sizeof(double) * nsys, 64));
+    int *h_status = (int *)((char *)h_ns + align_up(sizeof(long long) * nsys, 64));
+    memcpy(hsys, sh.sys.data(), sizeof(SysDesc) * nsys);
+    cudaStream_t st;
+    if ((rc = work_stream(p, &st))) return rc;
+    const cudaMemcpyKind in_kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind out_kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+
+    // inputs into the workspace (outside any graph: the caller's pointers vary)
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.sys, hsys, sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.xyz, all->xyz, sizeof(double) * 3 * sh.n_total, in_kind, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.q, all->q, sizeof(double) * sh.n_total, in_kind, st));
+
+    const bool want_f = forces != nullptr, want_p = pot != nullptr;
+    const bool graphs = p->use_graphs && !p->profile;
+    if (graphs) {
+        std::vector<long long> key = {prec, nsys, want_f, want_p, (long long)(uintptr_t)p->ws_mem};
+        key.insert(key.end(), n.begin(), n.end());
+        if (!p->graph_exec || key != p->graph_key) {
+            if (p->graph_exec) {
+                cudaGraphExecDestroy(p->graph_exec);
+                p->graph_exec = nullptr;
+            }
+            long long before = g_launches.load();
+            HSMA_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_update(p, sh, w, prec, want_f, want_p, st);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (rc || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                if (!rc) set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+                return rc ? rc : HSMA_E_CUDA;
+            }
+            ce = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) {
+                set_last_cuda_error(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
+                p->graph_exec = nullptr;
+                return HSMA_E_CUDA;
+            }
+            p->graph_kernels = g_launches.load() - before;
+            g_launches.fetch_sub(p->graph_kernels);  // counted when replayed
+            p->graph_key = key;
+        }
+        HSMA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, st));
+        g_launches.fetch_add(p->graph_kernels);
+    } else {
+        if ((rc = enqueue_update(p, sh, w, prec, want_f, want_p, st))) return rc;
+    }
+
     HSMA_CUDA_TRY(cudaMemcpyAsync(h_energy, w.energy, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaMemcpyAsync(h_status, w.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaMemcpyAsync(h_ns, w.ns, sizeof(long long) * nsys, cudaMemcpyDeviceToHost, st));
-    if (!on_dev && forces)
-        HSMA_CUDA_TRY(cudaMemcpyAsync(forces, w.forces, sizeof(double) * 3 * sh.n_total, cudaMemcpyDeviceToHost, st));
-    if (!on_dev && pot)
-        HSMA_CUDA_TRY(cudaMemcpyAsync(pot, w.pot, sizeof(double) * sh.n_total, cudaMemcpyDeviceToHost, st));
+    if (want_f) HSMA_CUDA_TRY(cudaMemcpyAsync(forces, w.forces, sizeof(double) * 3 * sh.n_total, out_kind, st));
+    if (want_p) HSMA_CUDA_TRY(cudaMemcpyAsync(pot, w.pot, sizeof(double) * sh.n_total, out_kind, st));
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));
     HSMA_CUDA_TRY(cudaGetLastError());
 
@@ -522,6 +592,23 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
 std::mutex g_scratch_mu;
 
 }  // namespace
+
+void hsma::plan_trim_workspace(hsma_plan_t p, size_t max_keep)
+{
+    if (!p || p->ws_cap <= max_keep || !p->ws_mem) return;
+    cudaStream_t st = p->stream ? p->stream : p->priv_stream;
+    if (st) cudaStreamSynchronize(st);
+    if (p->graph_exec) {
+        cudaGraphExecDestroy(p->graph_exec);
+        p->graph_exec = nullptr;
+        p->graph_key.clear();
+    }
+    cudaFree(p->ws_mem);
+    p->ws_mem = nullptr;
+    p->ws_cap = 0;
+    p->ws = Workspace();
+    p->last_nsys = 0;
+}
 
 extern "C" {
 
@@ -741,6 +828,10 @@ void hsma_plan_destroy(hsma_plan_t pl)
 {
     if (!pl) return;
     if (pl->stream || pl->ws_mem || pl->plan_mem) cudaStreamSynchronize(pl->stream);
+    if (pl->priv_stream) cudaStreamSynchronize(pl->priv_stream);
+    if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
+    if (pl->priv_stream) cudaStreamDestroy(pl->priv_stream);
+    if (pl->order_ev) cudaEventDestroy(pl->order_ev);
     if (pl->events_ready)
         for (int i = 0; i < 8; ++i) cudaEventDestroy(pl->ev[i]);
     if (pl->ws_mem) cudaFree(pl->ws_mem);

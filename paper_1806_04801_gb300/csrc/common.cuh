@@ -267,6 +267,10 @@ int launch_finalize(const SysDesc *sys, int nsys, const int *perm, const double 
                     const double *e_part, const double *phi_out, const double *e_out, double *forces, double *pot,
                     double *energy, int *status, cudaStream_t st);
 
+// api.cu: free a plan's workspace when it holds more than max_keep bytes
+// (used by the serving lanes to stay inside their memory budget).
+void plan_trim_workspace(hsma_plan_t plan, size_t max_keep);
+
 // tc_fit.cu
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
                   const void *Mp_lo, const double *Mrow, const double *phi_tgt, double *b_out, double *A,

@@ -477,17 +477,17 @@ int pair_max_ctas_per_sm(int precision)
     return n > 0 ? n : 1;
 }
 
+// The dynamic shared-memory attribute is set by pair_max_ctas_per_sm, which
+// every caller runs before its first launch (so that launches can be
+// captured into a CUDA graph).
 int launch_pair(const PairArgs &a, int precision, int grid, cudaStream_t st)
 {
     if (a.total_items <= 0) return HSMA_OK;
     size_t sm = pair_smem(precision);
-    if (precision == HSMA_FP64) {
-        HSMA_CUDA_TRY(cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (precision == HSMA_FP64)
         pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
-    } else {
-        HSMA_CUDA_TRY(cudaFuncSetAttribute(pair_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    else
         pair_fp32_kernel<<<grid, kThreads, sm, st>>>(a);
-    }
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

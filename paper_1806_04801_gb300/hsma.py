@@ -332,3 +332,90 @@ def basis(pts, p: int, Rs: float, stream=None):
     _check(_lib().hsma_basis(int(p), float(Rs), pts.shape[0], pp, out.data_ptr(), _stream_handle(stream)),
            "hsma_basis")
     return out
+
+
+# ------------------------------------------------------------------ serving
+class hsma_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("lanes", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class hsma_request_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("batch_size", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class hsma_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("elapsed_s", ctypes.c_double),
+                ("hbm_held_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+SIGNATURES.update({
+    "hsma_server_opts_default": (_I, [ctypes.POINTER(hsma_server_opts)]),
+    "hsma_server_create": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(_D), _I, _I, _D, _I, _I,
+                                ctypes.POINTER(hsma_server_opts)]),
+    "hsma_server_submit": (_I, [_VP, _I64, _VP, _VP, ctypes.POINTER(_I64)]),
+    "hsma_server_result": (_I, [_VP, _I64, _I, ctypes.POINTER(_D), _VP, ctypes.POINTER(hsma_request_info)]),
+    "hsma_server_stats": (_I, [_VP, ctypes.POINTER(hsma_server_stats_t)]),
+    "hsma_server_destroy": (None, [_VP]),
+})
+
+
+class Server:
+    """hsma_server_*: continuous-batching request loop over resident plans."""
+
+    def __init__(self, box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64, lanes: int = 2,
+                 max_batch: int = 64, hbm_budget_bytes: int = 0):
+        L = _lib()
+        o = hsma_server_opts()
+        _check(L.hsma_server_opts_default(ctypes.byref(o)), "hsma_server_opts_default")
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.lanes = int(lanes)
+        o.max_batch = int(max_batch)
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
+        h = ctypes.c_void_p()
+        _check(L.hsma_server_create(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon),
+                                    ctypes.byref(o)), "hsma_server_create")
+        self._h = h
+
+    def submit(self, xyz: np.ndarray, q: np.ndarray) -> int:
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        t = ctypes.c_int64()
+        _check(_lib().hsma_server_submit(self._h, q.shape[0], xyz.ctypes.data, q.ctypes.data, ctypes.byref(t)),
+               "hsma_server_submit")
+        return int(t.value)
+
+    def result(self, ticket: int, n: int | None = None, wait: bool = True, forces: bool = True):
+        """(code, energy, forces or None, info dict); code HSMA_E_AGAIN (-10)
+        when not ready and wait is False."""
+        e = ctypes.c_double()
+        info = hsma_request_info()
+        f = np.empty((n, 3)) if (forces and n) else None
+        code = _lib().hsma_server_result(self._h, int(ticket), 1 if wait else 0, ctypes.byref(e),
+                                         f.ctypes.data if f is not None else None, ctypes.byref(info))
+        return code, e.value, f, {k: getattr(info, k) for k, _ in hsma_request_info._fields_}
+
+    def stats(self) -> dict:
+        st = hsma_server_stats_t()
+        _check(_lib().hsma_server_stats(self._h, ctypes.byref(st)), "hsma_server_stats")
+        return {k: getattr(st, k) for k, _ in hsma_server_stats_t._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().hsma_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

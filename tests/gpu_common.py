@@ -38,3 +38,19 @@ def assert_within(e, prec, what=""):
 def to_dev(*arrays):
     import torch
     return [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda() for a in arrays]
+
+
+# Self-image energy constant of a unit charge in a periodic cubic box of side
+# L under conducting surroundings: U_self = XI q^2 / (2 L).
+XI_CUBIC = -2.837297479
+
+
+def energy_floor(q, L=1.0):
+    """Energy scale of a periodic system below which |U| is a cancellation
+    of much larger terms: 1/2 |XI| sum q^2 / L.  Relative energy errors use
+    max(|U|, this) as the denominator."""
+    return 0.5 * abs(XI_CUBIC) * float(np.sum(np.asarray(q) ** 2)) / L
+
+
+def rel_energy_err(U, U_ref, q, L=1.0):
+    return abs(U - U_ref) / max(abs(U_ref), energy_floor(q, L))

@@ -1,0 +1,156 @@
+"""Batched and served update steps on the GPU.
+
+* the CUDA-graph path gives bit-identical results to direct launches;
+* a batch of uneven systems (the 256-box workload, full size) agrees with
+  the FP64 path system by system, and sampled systems agree with the oracle;
+* the serving loop returns, for a request submitted alone and the same
+  request submitted in a mix with concurrent traffic, the same result within
+  the reduced-precision tolerance; oversize requests fail cleanly.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from gpu_common import TOL, assert_within, energy_floor, errors, rel_energy_err, rms, to_dev
+from paper_1806_04801_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1806_04801_gb300 import build
+    build.build()
+
+
+def hs():
+    from paper_1806_04801_gb300 import hsma
+    return hsma
+
+
+def test_graph_and_direct_launches_agree():
+    w = I.SMALL_PERIODIC
+    xyz, q = I.small_periodic()
+    dx, dq = to_dev(xyz, q)
+    res = {}
+    for graphs in (False, True):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", use_graphs=graphs) as plan:
+            out = [plan.energy_forces(dx, dq) for _ in range(3)]
+            res[graphs] = out
+            for U, F, _, _ in out[1:]:
+                assert U == out[0][0] and bool((F == out[0][1]).all())
+            # a different shape re-captures, then the first shape still replays correctly
+            x2, q2 = I.uniform_pm1(700, w.box, seed_offset=61)
+            plan.energy_forces(*to_dev(x2, q2))
+            U3, F3, _, _ = plan.energy_forces(dx, dq)
+            assert U3 == out[0][0] and bool((F3 == out[0][1]).all())
+    assert res[True][0][0] == res[False][0][0]
+    assert bool((res[True][0][1] == res[False][0][1]).all())
+
+
+@pytest.fixture(scope="module")
+def batch256():
+    systems = I.batch_periodic()
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    return systems, xyz, q, off
+
+
+@pytest.mark.slow
+def test_batched_256_boxes_full_size(batch256):
+    systems, xyz, q, off = batch256
+    w = I.BATCH_PERIODIC
+    dx, dq = to_dev(xyz, q)
+    out = {}
+    for prec in ("fp32", "fp64"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            E, F, _, st = plan.energy_forces_batched(dx, dq, off)
+            assert np.all(st == 0)
+            out[prec] = (E, F.cpu().numpy())
+    E32, F32 = out["fp32"]
+    E64, F64 = out["fp64"]
+    # relative energy error; the denominator is floored at the self-image
+    # energy scale, because some random +-1 draws have energies that cancel to
+    # far below their natural size (e.g. U = -12 for 2542 charges)
+    rel = np.array([rel_energy_err(E32[i], E64[i], systems[i][1]) for i in range(len(systems))])
+    assert rel.max() <= 1e-6, (rel.max(), int(rel.argmax()))
+    # and systems of ordinary energy meet the plain relative bound
+    plain = np.array([abs(E64[i]) >= energy_floor(systems[i][1]) for i in range(len(systems))])
+    assert plain.sum() >= 64
+    assert (np.abs(E32 - E64) / np.abs(E64))[plain].max() <= 1e-6
+    for i in range(len(systems)):
+        sl = slice(off[i], off[i + 1])
+        assert rms(F32[sl] - F64[sl]) <= 1e-5 * rms(F64[sl]), i
+    # sampled systems against the oracle (smallest, largest)
+    from oracle import hsma as oh
+    F2, _ = oh.fib_from_points(w.Q)
+    oplan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    sizes = np.diff(off)
+    for i in (int(sizes.argmin()), int(sizes.argmax())):
+        sx, sq = systems[i]
+        sample = None if len(sq) < 3000 else np.linspace(0, len(sq) - 1, 40).astype(np.int64)
+        ref = oh.energy_forces(sx, sq, oplan, nthreads=16, sample=sample)
+        sl = slice(off[i], off[i + 1])
+        idx = ref["index"]
+        e = errors(F32[sl][idx], ref["forces"])
+        assert e["force_rms"] <= TOL["fp32"]["force_rms"], (i, e)
+        if sample is None:
+            assert rel_energy_err(E32[i], ref["energy"], sq) <= 1e-6
+
+
+def _mixed_traffic(server, systems, results):
+    for j, (sx, sq) in enumerate(systems):
+        t = server.submit(sx, sq)
+        results.append((j, t))
+
+
+def test_serving_alone_and_in_mix_agree():
+    w = I.SERVING_PERIODIC
+    target_x, target_q = I.uniform_pm1(12000, w.box, seed_offset=70)
+    others = [I.uniform_pm1(int(n), w.box, seed_offset=71 + i) for i, n in
+              enumerate([1000, 30000, 5000, 2000, 60000, 800, 15000, 4000, 9000, 3000])]
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=2, max_batch=8) as srv:
+        t = srv.submit(target_x, target_q)
+        code, E_alone, F_alone, info = srv.result(t, n=len(target_q))
+        assert code == 0 and info["batch_size"] == 1
+        # the same request inside concurrent traffic
+        tickets = []
+        th = threading.Thread(target=_mixed_traffic, args=(srv, others[:5], tickets))
+        th.start()
+        t2 = srv.submit(target_x, target_q)
+        _mixed_traffic(srv, others[5:], tickets)
+        th.join()
+        code, E_mix, F_mix, info2 = srv.result(t2, n=len(target_q))
+        assert code == 0
+        assert rel_energy_err(E_mix, E_alone, target_q) <= TOL["fp32"]["energy"]
+        assert rms(F_mix - F_alone) <= TOL["fp32"]["force_rms"] * rms(F_alone)
+        # every mixed request agrees with a direct single-system call
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+            for j, tk in tickets:
+                sx, sq = others[j]
+                code, E, F, inf = srv.result(tk, n=len(sq))
+                assert code == 0
+                U1, F1, _, _ = plan.energy_forces(sx, sq)
+                assert rel_energy_err(E, U1, sq) <= TOL["fp32"]["energy"]
+                assert rms(F - F1) <= TOL["fp32"]["force_rms"] * rms(F1)
+        st = srv.stats()
+        assert st["completed"] == 12 and st["failed"] == 0
+
+
+def test_serving_rejects_requests_beyond_budget():
+    w = I.SERVING_PERIODIC
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, lanes=1, hbm_budget_bytes=64 << 20) as srv:
+        big = I.uniform_pm1(200000, w.box, seed_offset=80)
+        small = I.uniform_pm1(1000, w.box, seed_offset=81)
+        tb = srv.submit(*big)
+        ts = srv.submit(*small)
+        code_b, _, _, _ = srv.result(tb, n=len(big[1]))
+        code_s, E, _, _ = srv.result(ts, n=len(small[1]))
+        assert code_b == -11
+        assert code_s == 0 and np.isfinite(E)
+        # a ticket is collected once
+        assert srv.result(ts, n=1)[0] == -9

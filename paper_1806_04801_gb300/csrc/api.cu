@@ -66,7 +66,7 @@ struct Workspace {
     double *b = nullptr, *A = nullptr;
     double2 *img = nullptr;
     double *phi_out = nullptr, *e_out = nullptr;
-    double *energy = nullptr;
+    double *energy = nullptr, *upart = nullptr;
     int *status = nullptr;
     int *ctrl = nullptr;                            // work counters
     SysDesc *sys = nullptr;
@@ -78,7 +78,7 @@ struct BatchShape {
     long long n_total = 0, cap_total = 0, cnt_total = 0, rec_total = 0, tgt_total = 0, hist_total = 0,
               tiles_total = 0, max_tiles = 0;
     int items = 0, surf_items = 0, nblk_max = 1;
-    long long max_tgt = 0;
+    long long max_tgt = 0, max_n = 0;
     std::vector<SysDesc> sys;
 };
 
@@ -96,6 +96,11 @@ struct hsma_plan_s {
     void *plan_mem = nullptr;
     double4_32a *mon64 = nullptr;
     float4 *mon_hi = nullptr, *mon_lo = nullptr;
+    // monitoring targets in spatial (Morton) order for the pair kernel
+    double4_32a *mon64_s = nullptr;
+    float4 *mon_hi_s = nullptr, *mon_lo_s = nullptr, *mon_boxes = nullptr;
+    int *mon_perm_d = nullptr, *mon_inv = nullptr;
+    std::vector<int> mon_perm;
     double *Mrow = nullptr, *Mp = nullptr, *Bq = nullptr, *norm = nullptr;
     double4_32a *dirs = nullptr;
     int4 *shifts = nullptr;
@@ -248,6 +253,7 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         surf += (n[s] + STB - 1) / STB;
         nblk_max = std::max(nblk_max, d.nblk);
         max_tgt = std::max(max_tgt, ntgt);
+        sh->max_n = std::max(sh->max_n, (long long)n[s]);
     }
     sh->n_total = part;
     sh->cap_total = src;
@@ -297,6 +303,7 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     w->phi_out = c.take<double>(sh.n_total);
     w->e_out = c.take<double>(3 * sh.n_total);
     w->energy = c.take<double>(sh.nsys);
+    w->upart = c.take<double>((size_t)sh.nsys * finalize_blocks(sh.max_n));
     w->status = c.take<int>(sh.nsys);
     w->ctrl = c.take<int>(8);
     w->sys = c.take<SysDesc>(sh.nsys);
@@ -411,13 +418,14 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.src_hi = w.src_hi;
     pa.src_lo = w.src_lo;
     pa.src64 = w.src64;
-    pa.ext_hi = p->mon_hi;
-    pa.ext_lo = p->mon_lo;
-    pa.ext64 = p->mon64;
+    pa.ext_hi = p->mon_hi_s;
+    pa.ext_lo = p->mon_lo_s;
+    pa.ext64 = p->mon64_s;
     pa.n_ext = p->nmon;
     pa.ext_field = 0;
     pa.ext_skip_zero = 0;
     pa.boxes = w.boxes;
+    pa.ext_boxes = w.boxes ? p->mon_boxes : nullptr;
     pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
     pa.next_item = w.ctrl;
@@ -432,10 +440,11 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
 
     // (c) fit
     if (prec == HSMA_FP32_TC_FIT)
-        rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt, w.b,
-                           w.A, w.tc_work, st);
+        rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
+                           p->mon_inv, w.b, w.A, w.tc_work, st);
     else
-        rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, w.b, w.A, st);
+        rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A,
+                             st);
     if (rc) return rc;
     record(p, st, 4);
 
@@ -446,8 +455,9 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
                                    w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st)))
         return rc;
     record(p, st, 6);
-    if ((rc = launch_finalize(w.sys, nsys, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
-                              want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, w.energy, w.status, st)))
+    if ((rc = launch_finalize(w.sys, nsys, sh.max_n, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
+                              want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, w.upart, w.energy, w.status,
+                              st)))
         return rc;
     record(p, st, 7);
     return HSMA_OK;
@@ -587,6 +597,48 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
         single->n_images = 6 * (p->F2 + 1);
     }
     return worst;
+}
+
+// Morton order of the monitoring targets (a 1024^3 grid over the sphere of
+// radius R0 that holds all of them), so that each block of targets the pair
+// kernel takes is a compact region and far source tiles skip the low words.
+int sort_monitor_targets(hsma_plan_s *p, cudaStream_t st)
+{
+    const int n = p->nmon;
+    std::vector<double4_32a> h(n);
+    HSMA_CUDA_TRY(cudaMemcpyAsync(h.data(), p->mon64, sizeof(double4_32a) * n, cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+    auto spread = [](unsigned v) {
+        unsigned long long x = v & 0x3ffu, r = 0;
+        for (int b = 0; b < 10; ++b) r |= ((x >> b) & 1ull) << (3 * b);
+        return r;
+    };
+    std::vector<unsigned long long> key(n);
+    const double lo = -p->R0 * 1.000001, w = 2.0 * p->R0 * 1.000001;
+    for (int i = 0; i < n; ++i) {
+        const double c[3] = {h[i].x, h[i].y, h[i].z};
+        unsigned cell[3];
+        for (int a = 0; a < 3; ++a) {
+            double f = (c[a] - lo) / w * 1024.0;
+            int k = (int)floor(f);
+            cell[a] = (unsigned)std::min(1023, std::max(0, k));
+        }
+        key[i] = spread(cell[0]) | (spread(cell[1]) << 1) | (spread(cell[2]) << 2);
+    }
+    p->mon_perm.resize(n);
+    for (int i = 0; i < n; ++i) p->mon_perm[i] = i;
+    std::stable_sort(p->mon_perm.begin(), p->mon_perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    std::vector<int> inv(n);
+    for (int k = 0; k < n; ++k) inv[p->mon_perm[k]] = k;
+    HSMA_CUDA_TRY(cudaMemcpyAsync(p->mon_perm_d, p->mon_perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(p->mon_inv, inv.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    int rc = launch_gather_targets(n, p->mon_perm_d, p->mon64, p->mon_hi, p->mon_lo, p->mon64_s, p->mon_hi_s,
+                                   p->mon_lo_s, st);
+    if (rc) return rc;
+    rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64), p->mon_boxes, st);
+    if (rc) return rc;
+    HSMA_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above go out of scope
+    return HSMA_OK;
 }
 
 std::mutex g_scratch_mu;
@@ -733,6 +785,12 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         pl->mon64 = c.take<double4_32a>(nmon);
         pl->mon_hi = c.take<float4>(nmon);
         pl->mon_lo = c.take<float4>(nmon);
+        pl->mon64_s = c.take<double4_32a>(nmon);
+        pl->mon_hi_s = c.take<float4>(nmon);
+        pl->mon_lo_s = c.take<float4>(nmon);
+        pl->mon_boxes = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
+        pl->mon_perm_d = c.take<int>(nmon);
+        pl->mon_inv = c.take<int>(nmon);
         pl->Mrow = c.take<double>((size_t)K * ncols);
         pl->Mp = c.take<double>((size_t)ncols * K);
         pl->dirs = c.take<double4_32a>(ndir);
@@ -806,6 +864,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         // basis at Rs u_j == basis of the unit vector u_j with unit radius
         if ((rc = launch_basis(p, 1.0, ndir, (const double *)pl->dirs, 4, pl->norm, pl->Bq, Nb, st))) break;
         if ((rc = prepare_tc_operands(K, ncols, pl->Mp, pl->tc_hi, pl->tc_lo, st))) break;
+        if ((rc = sort_monitor_targets(pl, st))) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             rc = HSMA_E_CUDA;
             break;
@@ -967,6 +1026,12 @@ int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count
     }
     if (nd > count) return HSMA_E_ARG;
     HSMA_CUDA_TRY(cudaStreamSynchronize(pl->stream));
+    if (which == 2) {
+        std::vector<double> v(nd);
+        HSMA_CUDA_TRY(cudaMemcpy(v.data(), src, nd * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < nd; ++k) host_out[pl->mon_perm[k]] = v[k];
+        return nd;
+    }
     if (which == 3 || which == 4) {
         // particle values are held in spatial order; return them in caller order
         std::vector<double> v(nd);

@@ -206,6 +206,9 @@ struct SortArgs {
 int launch_sort_particles(const SortArgs &a, int nblk_max, cudaStream_t st);
 int launch_tile_boxes(const SysDesc *sys, int nsys, long long max_tiles, const long long *ns, const float4 *src_hi,
                       int tile, float4 *boxes, cudaStream_t st);
+int launch_gather_targets(int n, const int *perm, const double4_32a *in64, const float4 *inhi, const float4 *inlo,
+                          double4_32a *out64, float4 *outhi, float4 *outlo, cudaStream_t st);
+int launch_array_boxes(int n, const float4 *hi, int block, float4 *boxes, cudaStream_t st);
 
 // inset.cu
 struct InsetArgs {
@@ -243,6 +246,7 @@ struct PairArgs {
     int ext_field;          // external targets also need the field
     int ext_skip_zero;      // skip pairs at distance exactly zero for external targets
     const float4 *boxes = nullptr;  // FP32 form: box of every source tile (lo, hi), or null
+    const float4 *ext_boxes = nullptr;  // box of every block of external targets, or null
     float far2 = 0.f;               // tiles at least sqrt(far2) from the target block skip the low words
     float4 *partials;       // 2 x float4 (FP32) or 1 x double4_32a (FP64) per record
     int *next_item;
@@ -255,17 +259,20 @@ int launch_partial_reduce(const SysDesc *sys, int nsys, long long max_tgt, int n
                           int precision, double *phi_tgt, double *e_part, cudaStream_t st);
 
 // fit_surface.cu
+// mon_inv[i]: slot of monitoring target i among the (spatially ordered)
+// external targets the pair kernel used, or null for the identity.
 int launch_fit_fp64(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const double *Mp,
-                    const double *phi_tgt, double *b_out, double *A, cudaStream_t st);
+                    const double *phi_tgt, const int *mon_inv, double *b_out, double *A, cudaStream_t st);
 int launch_surface_charges(int nsys, int ndir, int Nb, const double *Bq, const double4_32a *dirs, const double *A,
                            double Rs, double2 *img, cudaStream_t st);
 int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const long long *ns, const float4 *src_hi,
                          const float4 *src_lo, const double4_32a *src64, int ndir, const double4_32a *dirs,
                          const double2 *img, double Rs, double dr, int precision, double *phi_out,
                          double *e_out, cudaStream_t st);
-int launch_finalize(const SysDesc *sys, int nsys, const int *perm, const double *q, const double *phi_tgt,
-                    const double *e_part, const double *phi_out, const double *e_out, double *forces, double *pot,
-                    double *energy, int *status, cudaStream_t st);
+int finalize_blocks(long long max_n);
+int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *perm, const double *q,
+                    const double *phi_tgt, const double *e_part, const double *phi_out, const double *e_out,
+                    double *forces, double *pot, double *upart, double *energy, int *status, cudaStream_t st);
 
 // api.cu: free a plan's workspace when it holds more than max_keep bytes
 // (used by the serving lanes to stay inside their memory budget).
@@ -273,8 +280,8 @@ void plan_trim_workspace(hsma_plan_t plan, size_t max_keep);
 
 // tc_fit.cu
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
-                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, double *b_out, double *A,
-                  float *work, cudaStream_t st);
+                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, const int *mon_inv, double *b_out,
+                  double *A, float *work, cudaStream_t st);
 int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *Mp_lo, cudaStream_t st);
 size_t tc_operand_bytes(int K, int ncols);
 size_t tc_work_bytes(int K, int ncols, int nsys);

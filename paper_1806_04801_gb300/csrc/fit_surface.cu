@@ -20,8 +20,16 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+__device__ __forceinline__ double rhs_at(const double *ph, const int *inv, int K, int i, bool periodic)
+{
+    const int a = inv ? inv[i] : i;
+    if (!periodic) return -ph[a];
+    const int b = inv ? inv[K + i] : K + i;
+    return ph[b] - ph[a];
+}
+
 __global__ void fit_fp64_kernel(const SysDesc *sys, int bc, int K, int ncols, int Nb, const double *Mp,
-                                const double *phi_tgt, double *b_out, double *A)
+                                const double *phi_tgt, const int *mon_inv, double *b_out, double *A)
 {
     const SysDesc sd = sys[blockIdx.y];
     const double *ph = phi_tgt + sd.tgt_off + sd.n;  // monitoring targets
@@ -29,19 +37,14 @@ __global__ void fit_fp64_kernel(const SysDesc *sys, int bc, int K, int ncols, in
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * (blockDim.x >> 5) + warp;
     if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < K; i += blockDim.x) {
-            double b = drop ? ph[K + i] - ph[i] : -ph[i];
-            b_out[(long long)blockIdx.y * K + i] = b;
-        }
+        for (int i = threadIdx.x; i < K; i += blockDim.x)
+            b_out[(long long)blockIdx.y * K + i] = rhs_at(ph, mon_inv, K, i, drop != 0);
         if (drop && threadIdx.x == 0) A[(long long)blockIdx.y * Nb] = 0.0;
     }
     if (c >= ncols) return;
     const double *row = Mp + (long long)c * K;
     double s = 0.0;
-    for (int i = lane; i < K; i += 32) {
-        double b = drop ? ph[K + i] - ph[i] : -ph[i];
-        s += row[i] * b;
-    }
+    for (int i = lane; i < K; i += 32) s += row[i] * rhs_at(ph, mon_inv, K, i, drop != 0);
     s = warp_sum(s);
     if (lane == 0) A[(long long)blockIdx.y * Nb + c + drop] = s;
 }
@@ -267,20 +270,25 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
     }
 }
 
-// Per system: forces, potentials and U = 1/2 sum q_i phi_i (fixed order).
-// Target i of a system is its i-th particle in spatial order; perm maps it
-// back to the caller's index.
-__global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, const int *perm, const double *q,
-                                                        const double *phi_tgt, const double *e_part,
-                                                        const double *phi_out, const double *e_out, double *forces,
-                                                        double *pot, double *energy, int *status)
+// Forces, potentials and per-block energy partials.  Target i of a system is
+// its i-th particle in spatial order; perm maps it back to the caller's index.
+// Block b of system s covers particles [b * kFinal, (b + 1) * kFinal).
+constexpr int kFinalThreads = 256;
+constexpr int kFinal = 2048;
+
+__global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const SysDesc *sys, const int *perm, const double *q,
+                                                                 const double *phi_tgt, const double *e_part,
+                                                                 const double *phi_out, const double *e_out,
+                                                                 double *forces, double *pot, double *upart,
+                                                                 int nb_max, int *status)
 {
     __shared__ double red[32];
-    const int s = blockIdx.x;
+    const int s = blockIdx.y;
     const SysDesc sd = sys[s];
+    const long long i0 = (long long)blockIdx.x * kFinal;
     double u = 0.0;
     bool bad = false;
-    for (long long i = threadIdx.x; i < sd.n; i += blockDim.x) {
+    for (long long i = i0 + threadIdx.x; i < sd.n && i < i0 + kFinal; i += blockDim.x) {
         long long t = sd.tgt_off + i, so = sd.part_off + i;
         long long o = sd.part_off + perm[so];
         double qi = q[o];
@@ -299,19 +307,29 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const SysDesc *sys, cons
     }
     if (bad) atomicOr(&status[s], ST_COINCIDENT);
     u = block_sum(u, red);
-    if (threadIdx.x == 0) {
-        energy[s] = 0.5 * u;
-        if (!isfinite(u)) atomicOr(&status[s], ST_COINCIDENT);
-    }
+    if (threadIdx.x == 0) upart[(long long)s * nb_max + blockIdx.x] = u;
+}
+
+// U = 1/2 sum of the block partials, in block order.
+__global__ void energy_kernel(const SysDesc *sys, const double *upart, int nb_max, double *energy, int *status)
+{
+    const int s = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    const SysDesc sd = sys[s];
+    const int nb = (int)((sd.n + kFinal - 1) / kFinal);
+    double u = 0.0;
+    for (int b = 0; b < nb; ++b) u += upart[(long long)s * nb_max + b];
+    energy[s] = 0.5 * u;
+    if (!isfinite(u)) atomicOr(&status[s], ST_COINCIDENT);
 }
 
 }  // namespace
 
 int launch_fit_fp64(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const double *Mp,
-                    const double *phi_tgt, double *b_out, double *A, cudaStream_t st)
+                    const double *phi_tgt, const int *mon_inv, double *b_out, double *A, cudaStream_t st)
 {
     dim3 grid((ncols + 7) / 8, nsys);
-    fit_fp64_kernel<<<grid, 256, 0, st>>>(sys, bc, K, ncols, Nb, Mp, phi_tgt, b_out, A);
+    fit_fp64_kernel<<<grid, 256, 0, st>>>(sys, bc, K, ncols, Nb, Mp, phi_tgt, mon_inv, b_out, A);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;
@@ -347,12 +365,17 @@ int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const lo
     return HSMA_OK;
 }
 
-int launch_finalize(const SysDesc *sys, int nsys, const int *perm, const double *q, const double *phi_tgt,
-                    const double *e_part, const double *phi_out, const double *e_out, double *forces, double *pot,
-                    double *energy, int *status, cudaStream_t st)
+int finalize_blocks(long long max_n) { return (int)((max_n + kFinal - 1) / kFinal); }
+
+int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *perm, const double *q,
+                    const double *phi_tgt, const double *e_part, const double *phi_out, const double *e_out,
+                    double *forces, double *pot, double *upart, double *energy, int *status, cudaStream_t st)
 {
-    finalize_kernel<<<nsys, 1024, 0, st>>>(sys, perm, q, phi_tgt, e_part, phi_out, e_out, forces, pot, energy,
-                                           status);
+    const int nb_max = finalize_blocks(max_n);
+    finalize_kernel<<<dim3(nb_max, nsys), kFinalThreads, 0, st>>>(sys, perm, q, phi_tgt, e_part, phi_out, e_out,
+                                                                  forces, pot, upart, nb_max, status);
+    HSMA_LAUNCHED();
+    energy_kernel<<<nsys, 32, 0, st>>>(sys, upart, nb_max, energy, status);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

@@ -188,11 +188,12 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
 
         // box of this block's targets (= in-set tile `tb`, its particles), for
         // the near/far decision per source tile
-        const bool use_boxes = part && a.boxes != nullptr;
+        const bool use_boxes = a.boxes != nullptr && (part || a.ext_boxes != nullptr);
         float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
         if (use_boxes) {
-            blo = a.boxes[2 * (sd.tile_off + it.tb)];
-            bhi = a.boxes[2 * (sd.tile_off + it.tb) + 1];
+            const float4 *bb = part ? a.boxes + 2 * (sd.tile_off + it.tb) : a.ext_boxes + 2 * (it.tb - sd.ntb_part);
+            blo = bb[0];
+            bhi = bb[1];
         }
         const float4 *gh = a.src_hi + sd.src_off;
         const float4 *gl = a.src_lo + sd.src_off;
@@ -253,7 +254,9 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
                 else
                     tile32<true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             } else {
-                if (skip == 2)
+                if (far)
+                    tile32<false, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                else if (skip == 2)
                     tile32<false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
                     tile32<false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);

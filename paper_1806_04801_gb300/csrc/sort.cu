@@ -207,3 +207,69 @@ int launch_tile_boxes(const SysDesc *sys, int nsys, long long max_tiles, const l
 }
 
 }  // namespace hsma
+
+namespace hsma {
+
+namespace {
+
+// out[k] = in[perm[k]] for the three monitoring-target arrays.
+__global__ void gather_targets_kernel(int n, const int *perm, const double4_32a *in64, const float4 *inhi,
+                                      const float4 *inlo, double4_32a *out64, float4 *outhi, float4 *outlo)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = perm[k];
+    out64[k] = in64[i];
+    outhi[k] = inhi[i];
+    outlo[k] = inlo[i];
+}
+
+// Box of every run of `block` consecutive points of an array (high words,
+// widened like the tile boxes).
+__global__ void array_boxes_kernel(int n, const float4 *hi, int block, float4 *boxes)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int nb = (n + block - 1) / block;
+    if (warp >= nb) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hh[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = warp * block + lane; i < min(n, (warp + 1) * block); i += 32) {
+        float4 p = hi[i];
+        lo[0] = fminf(lo[0], p.x); hh[0] = fmaxf(hh[0], p.x);
+        lo[1] = fminf(lo[1], p.y); hh[1] = fmaxf(hh[1], p.y);
+        lo[2] = fminf(lo[2], p.z); hh[2] = fmaxf(hh[2], p.z);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int ax = 0; ax < 3; ++ax) {
+            lo[ax] = fminf(lo[ax], __shfl_xor_sync(0xffffffffu, lo[ax], o));
+            hh[ax] = fmaxf(hh[ax], __shfl_xor_sync(0xffffffffu, hh[ax], o));
+        }
+    if (lane == 0) {
+        const float m = 1e-6f;
+        boxes[2 * warp] = make_float4(lo[0] - m * fabsf(lo[0]) - 1e-30f, lo[1] - m * fabsf(lo[1]) - 1e-30f,
+                                      lo[2] - m * fabsf(lo[2]) - 1e-30f, 0.f);
+        boxes[2 * warp + 1] = make_float4(hh[0] + m * fabsf(hh[0]) + 1e-30f, hh[1] + m * fabsf(hh[1]) + 1e-30f,
+                                          hh[2] + m * fabsf(hh[2]) + 1e-30f, 0.f);
+    }
+}
+
+}  // namespace
+
+int launch_gather_targets(int n, const int *perm, const double4_32a *in64, const float4 *inhi, const float4 *inlo,
+                          double4_32a *out64, float4 *outhi, float4 *outlo, cudaStream_t st)
+{
+    gather_targets_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, perm, in64, inhi, inlo, out64, outhi, outlo);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_array_boxes(int n, const float4 *hi, int block, float4 *boxes, cudaStream_t st)
+{
+    int nb = (n + block - 1) / block;
+    array_boxes_kernel<<<(nb * 32 + 127) / 128, 128, 0, st>>>(n, hi, block, boxes);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+}  // namespace hsma

@@ -36,7 +36,7 @@ __global__ void split_matrix_kernel(int K, int ncols, int Kp, int np, const doub
 
 // b_s from the monitoring potentials, stored FP64 and split into BF16 columns.
 __global__ void rhs_kernel(const SysDesc *sys, int nsys, int bc, int K, int Kp, const double *phi_tgt,
-                           double *b_out, __nv_bfloat16 *bhi, __nv_bfloat16 *blo)
+                           const int *inv, double *b_out, __nv_bfloat16 *bhi, __nv_bfloat16 *blo)
 {
     int s = blockIdx.y;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,7 +45,11 @@ __global__ void rhs_kernel(const SysDesc *sys, int nsys, int bc, int K, int Kp, 
     if (s < nsys && i < K) {
         const SysDesc sd = sys[s];
         const double *ph = phi_tgt + sd.tgt_off + sd.n;
-        b = (bc == HSMA_BC_PERIODIC) ? ph[K + i] - ph[i] : -ph[i];
+        const int a = inv ? inv[i] : i;
+        if (bc == HSMA_BC_PERIODIC)
+            b = ph[inv ? inv[K + i] : K + i] - ph[a];
+        else
+            b = -ph[a];
         b_out[(long long)s * K + i] = b;
     }
     split_bf16(b, bhi[(long long)s * Kp + i], blo[(long long)s * Kp + i]);
@@ -154,8 +158,8 @@ int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *M
 }
 
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
-                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, double *b_out, double *A, float *work,
-                  cudaStream_t st)
+                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, const int *mon_inv, double *b_out,
+                  double *A, float *work, cudaStream_t st)
 {
     const int Kp = pad16(K), np = pad16(ncols), ns8 = pad8(nsys);
     char *w = (char *)work;
@@ -173,7 +177,7 @@ int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb
     double *A1 = (double *)take((size_t)ncols * nsys * 8);
     const __nv_bfloat16 *ahi = (const __nv_bfloat16 *)Mp_hi, *alo = (const __nv_bfloat16 *)Mp_lo;
     dim3 g1((Kp + 255) / 256, ns8);
-    rhs_kernel<<<g1, 256, 0, st>>>(sys, nsys, bc, K, Kp, phi_tgt, b_out, bhi, blo);
+    rhs_kernel<<<g1, 256, 0, st>>>(sys, nsys, bc, K, Kp, phi_tgt, mon_inv, b_out, bhi, blo);
     HSMA_LAUNCHED();
     const int warps = (np / 16) * (ns8 / 8);
     tc_gemm_kernel<<<(warps + 3) / 4, 128, 0, st>>>(Kp, np, ns8, ahi, alo, bhi, blo, C1);

@@ -102,10 +102,10 @@ def test_batched_256_boxes_full_size(batch256):
             assert rel_energy_err(E32[i], ref["energy"], sq) <= 1e-6
 
 
-def _mixed_traffic(server, systems, results):
+def _mixed_traffic(server, systems, first, results):
     for j, (sx, sq) in enumerate(systems):
         t = server.submit(sx, sq)
-        results.append((j, t))
+        results.append((first + j, t))
 
 
 def test_serving_alone_and_in_mix_agree():
@@ -119,10 +119,10 @@ def test_serving_alone_and_in_mix_agree():
         assert code == 0 and info["batch_size"] == 1
         # the same request inside concurrent traffic
         tickets = []
-        th = threading.Thread(target=_mixed_traffic, args=(srv, others[:5], tickets))
+        th = threading.Thread(target=_mixed_traffic, args=(srv, others[:5], 0, tickets))
         th.start()
         t2 = srv.submit(target_x, target_q)
-        _mixed_traffic(srv, others[5:], tickets)
+        _mixed_traffic(srv, others[5:], 5, tickets)
         th.join()
         code, E_mix, F_mix, info2 = srv.result(t2, n=len(target_q))
         assert code == 0

@@ -36,6 +36,11 @@ OPS_POT_FIELD = 13               # FP32 lane instructions per potential+field pa
 OPS_POT = 7                      # FP32 lane instructions per potential-only pair
 RECIPE_SMS = 152
 RECIPE_MAX_SM_MHZ = 2070.0
+# DRAM bytes (read + write) of one full-size pair_fp32_kernel launch of the
+# periodic N=100000 workload, from the ncu capture summarised in
+# profiles/pair_fp32_kernel_periodic_N100000_dram.md (current kernel build).
+PAIR_FP32_TRAFFIC_BYTES = {100_000: 237.46e6}
+OPS_SURFACE = 45                 # FP32 lane instructions per particle-direction pair of the surface kernel
 
 
 def parse():
@@ -369,7 +374,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        pair_ms.append(plan.last_timings()[1])
+        phases = plan.last_timings()
+        pair_ms.append(phases[1])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = hsma.kernel_launches() - launches0
@@ -458,17 +464,23 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "kernel": "pair_fp32_kernel" if args.precision != "fp64" else "pair_fp64_kernel",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "T FP32 lane-instructions/s", "frac": achieved / peak_ops, "traffic": None,
+                     "unit": "T FP32 lane-instructions/s", "frac": achieved / peak_ops,
+                     "traffic": (PAIR_FP32_TRAFFIC_BYTES.get(n) if args.precision == "fp32" else None),
                      "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
                                    f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",
                      "kernel_ms": pair_avg_ms, "share_of_step": pair_avg_ms / ms_per_step},
+        "roofline_surface": {"bound": "alu", "kernel": "surface_pairs_fp32_kernel",
+                             "achieved": OPS_SURFACE * pairs_surf / (phases[5] / 1000.0) / 1e12,
+                             "peak": peak_ops / 1e12, "unit": "T FP32 lane-instructions/s",
+                             "frac": OPS_SURFACE * pairs_surf / (phases[5] / 1000.0) / peak_ops,
+                             "kernel_ms": phases[5]},
         "e2e": {"value": 1000.0 / e2e_step, "unit": "systems/s", "ms_per_step": e2e_step,
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": n * 24 + 8},
         "gpu_launches": int(launches),
         "clocks": clk,
         "phases_ms": dict(zip(["inset", "near_field", "chunk_reduce", "fit", "surface_charges", "surface_pairs",
-                               "finalize", "total"], plan.last_timings())),
+                               "finalize", "total"], phases)),
         "accuracy": accuracy,
         "workloads": extras,
         "cpu_baseline": cpu,

@@ -5,6 +5,7 @@
 // work on the plan's stream.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -89,6 +90,7 @@ struct hsma_plan_s {
     int bc, P, Nb, ncols, K, nmon, F2, F1, ndir, nshifts;
     double Rs, R0, dr, alpha, cond;
     double far_rel = 1.0 / 15.0;  // near/far threshold of the FP32 pair sums, in units of Rs
+    int stall_test = 0;           // HSMA_TEST_STALL_WAIT=1 at plan creation: exercise the timeout path
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
     int num_sms, ctas[3];
@@ -426,6 +428,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.ext_skip_zero = 0;
     pa.boxes = w.boxes;
     pa.ext_boxes = w.boxes ? p->mon_boxes : nullptr;
+    pa.stall_test = p->stall_test;
     pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
     pa.next_item = w.ctrl;
@@ -747,6 +750,10 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     pl->use_graphs = o.use_graphs;
     pl->profile = o.profile;
     pl->stream = (cudaStream_t)o.stream;
+    {
+        const char *e = getenv("HSMA_TEST_STALL_WAIT");
+        pl->stall_test = (e && e[0] == '1') ? 1 : 0;
+    }
 
     int rc = HSMA_OK;
     auto fail = [&](int code) {

@@ -247,6 +247,7 @@ struct PairArgs {
     int ext_skip_zero;      // skip pairs at distance exactly zero for external targets
     const float4 *boxes = nullptr;  // FP32 form: box of every source tile (lo, hi), or null
     const float4 *ext_boxes = nullptr;  // box of every block of external targets, or null
+    int stall_test = 0;             // test hook: wait on a barrier nothing arrives at (bounded)
     float far2 = 0.f;               // tiles at least sqrt(far2) from the target block skip the low words
     float4 *partials;       // 2 x float4 (FP32) or 1 x double4_32a (FP64) per record
     int *next_item;

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
                 float Ai = rsqrt_sfu(A2);
                 float Bi = rsqrt_sfu(B2);
                 float Aa = A2 * Ai, Bb = B2 * Bi;
-                float inv_sum = 1.f / (Aa + Bb);
+                float inv_sum = __fdividef(1.f, Aa + Bb);
                 float qs = u.w * ri;
                 float dip = -2.f * p * ad * Ai * Bi * inv_sum;
                 pa[t] += qs + dip;

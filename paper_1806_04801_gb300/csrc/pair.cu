@@ -126,17 +126,25 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
     extern __shared__ __align__(128) float4 smem32[];
     float4 *sh_hi = smem32;                // [2][kTile32]
     float4 *sh_lo = smem32 + 2 * kTile32;  // [2][kTile32]
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[3];
     __shared__ int s_item, s_abort;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
         mbar_fence_init();
         s_abort = 0;
     }
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
+    if (a.stall_test) {
+        // Test of the bounded-wait path: bar[2] never completes a phase (no
+        // arrival, no copy), so the wait runs out after ~1e6 cycles, the
+        // status records a timeout and the CTA returns.
+        if (!mbar_wait_bounded(&bar[2], 0u, 1000000LL)) atomicOr(&a.status[0], ST_TIMEOUT);
+        return;
+    }
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.next_item, 1);

@@ -268,3 +268,41 @@ def test_large_periodic_sampled_full_size():
     U32, U64 = res["fp32"][0], res["fp64"][0]
     assert abs(U32 - U64) <= 1e-6 * abs(U64)
     assert rms(res["fp32"][1] - res["fp64"][1]) <= 1e-5 * rms(res["fp64"][1])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["fp32_tc", "fp64"])
+def test_grounded_cavity_full_size(prec):
+    """The 1x1x2 conducting cavity at full size (20000 charges, p = 10,
+    Kmon = 1500, Q = 6000): energy against the oracle's full energy, forces on
+    sampled particles."""
+    w = I.GROUNDED_CAVITY
+    xyz, q = I.grounded_cavity()
+    from oracle import hsma as oh
+    F2, _ = oh.fib_from_points(w.Q)
+    oplan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    ref = oh.energy_forces(xyz, q, oplan, nthreads=16)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+        U, F, pot, ns = plan.energy_forces(*to_dev(xyz, q), potentials=True)
+        assert ns == ref["n_inset"]
+        e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+        assert_within(e, prec, "grounded full size")
+
+
+@pytest.mark.slow
+def test_large_periodic_fp64_full_energy():
+    """The benchmarked periodic workload (100000 charges): the FP64 GPU energy
+    against the oracle's full FP64 energy (1.4e11 pairs on the host cores)."""
+    import os
+    w = I.LARGE_PERIODIC
+    xyz, q = I.large_periodic()
+    from oracle import hsma as oh
+    F2, _ = oh.fib_from_points(w.Q)
+    oplan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    ref = oh.energy_forces(xyz, q, oplan, nthreads=os.cpu_count() or 16)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as plan:
+        U, F, _, _ = plan.energy_forces(*to_dev(xyz, q))
+    assert_within(errors(F.cpu().numpy(), ref["forces"], U, ref["energy"]), "fp64", "periodic 1e5 full")
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        U32, F32, _, _ = plan.energy_forces(*to_dev(xyz, q))
+    assert_within(errors(F32.cpu().numpy(), ref["forces"], U32, ref["energy"]), "fp32", "periodic 1e5 full")

@@ -72,19 +72,26 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
     off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
     dx = torch.as_tensor(xyz).cuda()
     dq = torch.as_tensor(q).cuda()
-    for _ in range(warmup):
-        plan_fp32.energy_forces_batched(dx, dq, off)
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        E32, F32, _, st = plan_fp32.energy_forces_batched(dx, dq, off)
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-    ms = float(np.median(times))
+
+    def timed():
+        for _ in range(warmup):
+            plan_fp32.energy_forces_batched(dx, dq, off)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            E, F, _, st = plan_fp32.energy_forces_batched(dx, dq, off)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return float(np.median(times)), E
+    plan_fp32.set_tuning(4, 24)
+    ms_default, _ = timed()
+    plan_fp32.set_tuning(None, None)
+    tuning = plan_fp32.autotune(dx, dq, off)
+    ms, E32 = timed()
     # the plain paths: one system per call (FP64, and FP32 for reference), on
     # a sample of systems
     rng = np.random.default_rng(0)
@@ -118,6 +125,7 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
     t32_all = t32 * w_all / w_pick
     return {"workload": "batched-256-periodic-p10 (N log-uniform in [500, 50000], +-1)",
             "systems": len(systems), "particles": int(off[-1]), "ms_per_batch": ms,
+            "autotuned": tuning, "ms_per_batch_default_tiles": ms_default,
             "systems_per_s": len(systems) / (ms / 1000.0),
             "fp64_one_system_per_launch_systems_per_s": len(systems) / (t64_all / 1000.0),
             "fp32_one_system_per_launch_systems_per_s": len(systems) / (t32_all / 1000.0),
@@ -351,6 +359,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    tuning = plan.autotune(dx, dq)
     for _ in range(args.warmup):
         plan.energy_forces(dx, dq)
     torch.cuda.synchronize()
@@ -459,6 +468,7 @@ def main():
         "latency_ms": {"p50": float(np.percentile(step_sorted, 50)), "p99": float(np.percentile(step_sorted, 99))},
         "config": {"workload": w.name, "N": n, "p": w.p, "Kmon": w.Kmon, "Q": w.Q, "F2": info["F2"],
                    "N_o": info["n_images"], "Rs": w.R, "N_s": int(n_inset), "precision": args.precision,
+                   "autotuned": tuning,
                    "pairs_per_step": {"pot_field": pairs_pf, "pot_only_monitor": pairs_p, "surface": pairs_surf},
                    "l2": "flushed between timed steps (256 MB write, outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -183,6 +183,45 @@ int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offset
                                const hsma_particles *all, double *energies, double *forces,
                                double *potentials, int *status);
 
+/* ----------------------------------------------------------------- tuning */
+/* Work decomposition of the near-field pair kernel (no counterpart in the
+ * paper; it changes speed, not results beyond rounding of the chunk
+ * grouping):
+ *   pair_variant    targets per thread of the FP32 kernel: 4 (blocks and
+ *                   source tiles of 512) or 2 (256: more CTAs per SM, finer
+ *                   work items); ignored in FP64
+ *   items_per_slot  work items per resident CTA slot (source chunks are sized
+ *                   so that a call has about this many items per slot)
+ *   ms              time measured by hsma_autotune (0 otherwise)
+ * Defaults: 4 and 24. */
+typedef struct {
+    int pair_variant;
+    int items_per_slot;
+    double ms;
+} hsma_tuning;
+
+/* Use *t for every later call (NULL: choose per call from the entries that
+ * hsma_autotune / hsma_plan_load_tuning gave the plan for the call's work
+ * size, else the defaults). */
+int hsma_plan_set_tuning(hsma_plan_t plan, const hsma_tuning *t);
+
+/* The tuning a call with this batch shape (offsets as in
+ * hsma_energy_forces_batched, host array) would use. */
+int hsma_plan_get_tuning(hsma_plan_t plan, int nsys, const int64_t *offsets, hsma_tuning *out);
+
+/* Autotuner: runs the update step on this batch for each candidate
+ * (pair_variant 4 and 2, items_per_slot 8, 16, 24, 48), keeps the fastest as
+ * the plan's entry for this work size, returns it in *best, and appends it as
+ * one JSON line to cache_path (if not NULL).  Device inputs are recommended
+ * (host inputs add their copies to every timing). */
+int hsma_autotune(hsma_plan_t plan, int nsys, const int64_t *offsets, const hsma_particles *all,
+                  const char *cache_path, hsma_tuning *best);
+
+/* Loads the entries of a cache written by hsma_autotune that match this plan
+ * (device name, boundary, p, Kmon, F2, precision).  Returns how many were
+ * loaded (0 if the file does not exist), or a negative code. */
+int hsma_plan_load_tuning(hsma_plan_t plan, const char *cache_path);
+
 /* --------------------------------------------------------------- serving */
 /* A request loop with continuous batching (a deployment layer over the
  * update step; the paper has no serving component).  The server keeps

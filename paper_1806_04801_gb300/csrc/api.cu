@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <vector>
 
@@ -80,6 +81,7 @@ struct BatchShape {
               tiles_total = 0, max_tiles = 0;
     int items = 0, surf_items = 0, nblk_max = 1;
     long long max_tgt = 0, max_n = 0;
+    int variant = 4;
     std::vector<SysDesc> sys;
 };
 
@@ -93,14 +95,19 @@ struct hsma_plan_s {
     int stall_test = 0;           // HSMA_TEST_STALL_WAIT=1 at plan creation: exercise the timeout path
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
-    int num_sms, ctas[3];
+    int num_sms, ctas[3], ctas_v2;
+    // tuning of the pair kernel: a fixed choice, or entries per work bucket
+    bool tune_fixed = false;
+    hsma_tuning tune_value{4, 24, 0.0};
+    std::vector<std::pair<int, hsma_tuning>> tune_entries;  // (bucket, tuning)
+    char device_name[256] = {0};
     // plan-resident device data
     void *plan_mem = nullptr;
     double4_32a *mon64 = nullptr;
     float4 *mon_hi = nullptr, *mon_lo = nullptr;
     // monitoring targets in spatial (Morton) order for the pair kernel
     double4_32a *mon64_s = nullptr;
-    float4 *mon_hi_s = nullptr, *mon_lo_s = nullptr, *mon_boxes = nullptr;
+    float4 *mon_hi_s = nullptr, *mon_lo_s = nullptr, *mon_boxes = nullptr, *mon_boxes2 = nullptr;
     int *mon_perm_d = nullptr, *mon_inv = nullptr;
     std::vector<int> mon_perm;
     double *Mrow = nullptr, *Mp = nullptr, *Bq = nullptr, *norm = nullptr;
@@ -196,16 +203,54 @@ int ensure_pinned(hsma_plan_s *p, size_t bytes)
 
 // Work decomposition of a batch: targets per block, source chunks per system,
 // work items, surface blocks.  Pure host arithmetic.
-void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precision, BatchShape *sh)
+int tuned_ctas(const hsma_plan_s *p, int precision, int variant)
+{
+    if (precision == HSMA_FP64) return p->ctas[0];
+    return variant == 2 ? p->ctas_v2 : p->ctas[1];
+}
+
+// Pair work of a batch (targets x estimated in-set sources), and its bucket
+// (floor of log2) that keys the tuning entries.
+double batch_work(const hsma_plan_s *p, int nsys, const long long *n)
+{
+    const double vsphere = 4.0 / 3.0 * kPi * p->Rs * p->Rs * p->Rs;
+    const double vbox = p->L[0] * p->L[1] * p->L[2];
+    double w = 0.0;
+    for (int s = 0; s < nsys; ++s)
+        w += (double)(n[s] + p->nmon) * std::min((double)n[s] * p->nshifts, (double)n[s] * vsphere / vbox);
+    return w;
+}
+
+int work_bucket(double w) { return w > 1.0 ? (int)floor(log2(w)) : 0; }
+
+hsma_tuning choose_tuning(const hsma_plan_s *p, int nsys, const long long *n)
+{
+    if (p->tune_fixed) return p->tune_value;
+    const int b = work_bucket(batch_work(p, nsys, n));
+    const hsma_tuning *best = nullptr;
+    int bestd = 1 << 30;
+    for (auto &e : p->tune_entries) {
+        int d = abs(e.first - b);
+        if (d < bestd && d <= 1) {
+            bestd = d;
+            best = &e.second;
+        }
+    }
+    return best ? *best : hsma_tuning{4, 24, 0.0};
+}
+
+void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precision, const hsma_tuning &tu,
+                 BatchShape *sh)
 {
     sh->nsys = nsys;
     sh->sys.assign(nsys, SysDesc{});
-    const int TB = pair_targets_per_block(precision);
+    sh->variant = tu.pair_variant == 2 ? 2 : 4;
+    const int TB = pair_targets_per_block(precision, sh->variant);
     const int STB = surface_targets_per_block();
-    const int tile = (precision == HSMA_FP64) ? 256 : 512;
+    const int tile = TB;
     const double vsphere = 4.0 / 3.0 * kPi * p->Rs * p->Rs * p->Rs;
     const double vbox = p->L[0] * p->L[1] * p->L[2];
-    const int slots = p->num_sms * p->ctas[precision == HSMA_FP64 ? 0 : 1];
+    const int slots = p->num_sms * tuned_ctas(p, precision, sh->variant);
     const int ntb_mon = (p->nmon + TB - 1) / TB;
     double work = 0.0;
     std::vector<double> ns_est(nsys);
@@ -214,7 +259,7 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         int ntb = (int)((n[s] + TB - 1) / TB) + ntb_mon;
         work += (double)ntb * ns_est[s];
     }
-    const double items_wanted = 24.0 * slots;
+    const double items_wanted = (double)std::max(1, tu.items_per_slot) * slots;
     const double chunk = std::max(4.0 * tile, work / items_wanted);
     long long part = 0, src = 0, tgt = 0, rec = 0, cnt = 0, hist = 0, tiles = 0, max_tiles = 0;
     long long items = 0, surf = 0;
@@ -234,7 +279,7 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         int gb = 1;
         while (gb < 5 && (double)(1 << (3 * gb)) * 4.0 < (double)n[s]) ++gb;
         d.gbits = gb;
-        long long tcap = (n[s] * p->nshifts + tile - 1) / tile;
+        long long tcap = (n[s] * p->nshifts + 255) / 256;  // tiles of the smallest variant
         d.ntb_part = (int)((n[s] + TB - 1) / TB);
         d.ntb = d.ntb_part + ntb_mon;
         long long maxchunks = std::max(1LL, (long long)(ns_est[s] / tile));
@@ -408,7 +453,8 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     ia.src64 = w.src64;
     ia.status = w.status;
     if ((rc = launch_inset(ia, st))) return rc;
-    if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, 512, w.boxes, st))) return rc;
+    const int TB = pair_targets_per_block(prec, sh.variant);
+    if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
     record(p, st, 1);
 
     // (a2) near-field sums at particles and monitoring targets
@@ -427,15 +473,15 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.ext_field = 0;
     pa.ext_skip_zero = 0;
     pa.boxes = w.boxes;
-    pa.ext_boxes = w.boxes ? p->mon_boxes : nullptr;
+    pa.ext_boxes = w.boxes ? (sh.variant == 2 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
     pa.stall_test = p->stall_test;
     pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
     pa.next_item = w.ctrl;
     pa.status = w.status;
-    const int ctas = p->ctas[prec == HSMA_FP64 ? 0 : 1];
+    const int ctas = tuned_ctas(p, prec, sh.variant);
     const int grid = std::max(1, std::min(sh.items, p->num_sms * ctas));
-    if ((rc = launch_pair(pa, prec, grid, st))) return rc;
+    if ((rc = launch_pair(pa, prec, sh.variant, grid, st))) return rc;
     record(p, st, 2);
     if ((rc = launch_partial_reduce(w.sys, nsys, sh.max_tgt, p->nmon, w.partials, prec, w.phi_tgt, w.e_part, st)))
         return rc;
@@ -500,7 +546,7 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     const int prec = p->precision;
     const bool on_dev = all->on_device != 0;
     BatchShape sh;
-    shape_batch(p, nsys, n.data(), prec, &sh);
+    shape_batch(p, nsys, n.data(), prec, choose_tuning(p, nsys, n.data()), &sh);
     if (sh.items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
     Workspace w;
     size_t need = carve_workspace(p, sh, prec, true, true, nullptr, &w);
@@ -531,7 +577,8 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     const bool want_f = forces != nullptr, want_p = pot != nullptr;
     const bool graphs = p->use_graphs && !p->profile;
     if (graphs) {
-        std::vector<long long> key = {prec, nsys, want_f, want_p, (long long)(uintptr_t)p->ws_mem};
+        std::vector<long long> key = {prec, nsys, want_f, want_p, (long long)(uintptr_t)p->ws_mem, sh.variant,
+                                      (long long)sh.items};
         key.insert(key.end(), n.begin(), n.end());
         if (!p->graph_exec || key != p->graph_key) {
             if (p->graph_exec) {
@@ -638,7 +685,9 @@ int sort_monitor_targets(hsma_plan_s *p, cudaStream_t st)
     int rc = launch_gather_targets(n, p->mon_perm_d, p->mon64, p->mon_hi, p->mon_lo, p->mon64_s, p->mon_hi_s,
                                    p->mon_lo_s, st);
     if (rc) return rc;
-    rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64), p->mon_boxes, st);
+    rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64, 4), p->mon_boxes, st);
+    if (rc) return rc;
+    rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64, 2), p->mon_boxes2, st);
     if (rc) return rc;
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above go out of scope
     return HSMA_OK;
@@ -769,7 +818,9 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return fail(HSMA_E_CUDA);
     pl->num_sms = prop.multiProcessorCount;
     pl->ctas[0] = pair_max_ctas_per_sm(HSMA_FP64);
-    pl->ctas[1] = pl->ctas[2] = pair_max_ctas_per_sm(HSMA_FP32_ACC64);
+    pl->ctas[1] = pl->ctas[2] = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 4);
+    pl->ctas_v2 = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 2);
+    snprintf(pl->device_name, sizeof(pl->device_name), "%s", prop.name);
 
     // image shift table: k = 0 first, then lexicographic (kx, ky, kz)
     int Ks[3];
@@ -796,6 +847,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         pl->mon_hi_s = c.take<float4>(nmon);
         pl->mon_lo_s = c.take<float4>(nmon);
         pl->mon_boxes = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
+        pl->mon_boxes2 = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
         pl->mon_perm_d = c.take<int>(nmon);
         pl->mon_inv = c.take<int>(nmon);
         pl->Mrow = c.take<double>((size_t)K * ncols);
@@ -949,7 +1001,7 @@ int hsma_plan_footprint(hsma_plan_t pl, int64_t n, size_t *bytes)
     if (!pl || !bytes || n < 1) return HSMA_E_ARG;
     BatchShape sh;
     long long nn = n;
-    shape_batch(pl, 1, &nn, pl->precision, &sh);
+    shape_batch(pl, 1, &nn, pl->precision, choose_tuning(pl, 1, &nn), &sh);
     Workspace w;
     *bytes = carve_workspace(pl, sh, pl->precision, true, true, nullptr, &w);
     return HSMA_OK;
@@ -1050,6 +1102,116 @@ int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count
     }
     HSMA_CUDA_TRY(cudaMemcpy(host_out, src, nd * sizeof(double), cudaMemcpyDeviceToHost));
     return nd;
+}
+
+// ------------------------------------------------------------------ tuning
+int hsma_plan_set_tuning(hsma_plan_t pl, const hsma_tuning *t)
+{
+    if (!pl) return HSMA_E_ARG;
+    if (!t) {
+        pl->tune_fixed = false;
+        return HSMA_OK;
+    }
+    if ((t->pair_variant != 2 && t->pair_variant != 4) || t->items_per_slot < 1 || t->items_per_slot > 4096)
+        return HSMA_E_ARG;
+    pl->tune_fixed = true;
+    pl->tune_value = *t;
+    return HSMA_OK;
+}
+
+int hsma_plan_get_tuning(hsma_plan_t pl, int nsys, const int64_t *offsets, hsma_tuning *out)
+{
+    if (!pl || !out || nsys < 1 || !offsets) return HSMA_E_ARG;
+    std::vector<long long> n(nsys);
+    for (int s = 0; s < nsys; ++s) n[s] = offsets[s + 1] - offsets[s];
+    *out = choose_tuning(pl, nsys, n.data());
+    return HSMA_OK;
+}
+
+int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_particles *all,
+                  const char *cache_path, hsma_tuning *best)
+{
+    if (!pl || nsys < 1 || !offsets || !all) return HSMA_E_ARG;
+    std::vector<long long> n(nsys);
+    for (int s = 0; s < nsys; ++s) n[s] = offsets[s + 1] - offsets[s];
+    const bool fixed0 = pl->tune_fixed;
+    const hsma_tuning value0 = pl->tune_value;
+    std::vector<double> energies(nsys);
+    std::vector<hsma_tuning> cands;
+    const int variants[2] = {4, 2};
+    const int items[4] = {8, 16, 24, 48};
+    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 2); ++v)
+        for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
+    hsma_tuning win{4, 24, 1e300};
+    int rc = HSMA_OK;
+    for (auto &c : cands) {
+        pl->tune_fixed = true;
+        pl->tune_value = c;
+        double t_best = 1e300;
+        for (int rep = 0; rep < 3 && !rc; ++rep) {
+            auto t0 = std::chrono::steady_clock::now();
+            rc = run_update(pl, nsys, offsets, all, energies.data(), nullptr, nullptr, nullptr, nullptr);
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (rep > 0) t_best = std::min(t_best, ms);  // rep 0 warms the workspace and graph
+        }
+        if (rc) break;
+        c.ms = t_best;
+        if (t_best < win.ms) win = c;
+    }
+    pl->tune_fixed = fixed0;
+    pl->tune_value = value0;
+    if (rc) return rc;
+    const int bucket = work_bucket(batch_work(pl, nsys, n.data()));
+    bool replaced = false;
+    for (auto &e : pl->tune_entries)
+        if (e.first == bucket) {
+            e.second = win;
+            replaced = true;
+        }
+    if (!replaced) pl->tune_entries.push_back({bucket, win});
+    if (best) *best = win;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (!f) return HSMA_E_ARG;
+        fprintf(f,
+                "{\"device\":\"%s\",\"bc\":%d,\"p\":%d,\"Kmon\":%d,\"F2\":%d,\"precision\":%d,"
+                "\"bucket\":%d,\"pair_variant\":%d,\"items_per_slot\":%d,\"ms\":%.4f}\n",
+                pl->device_name, pl->bc, pl->P, pl->K, pl->F2, pl->precision, bucket, win.pair_variant,
+                win.items_per_slot, win.ms);
+        fclose(f);
+    }
+    return HSMA_OK;
+}
+
+int hsma_plan_load_tuning(hsma_plan_t pl, const char *cache_path)
+{
+    if (!pl || !cache_path) return HSMA_E_ARG;
+    FILE *f = fopen(cache_path, "r");
+    if (!f) return 0;
+    char line[1024], dev[256];
+    int loaded = 0;
+    while (fgets(line, sizeof(line), f)) {
+        int bc, P, K, F2, prec, bucket, var, ips;
+        double ms;
+        int got = sscanf(line,
+                         "{\"device\":\"%255[^\"]\",\"bc\":%d,\"p\":%d,\"Kmon\":%d,\"F2\":%d,\"precision\":%d,"
+                         "\"bucket\":%d,\"pair_variant\":%d,\"items_per_slot\":%d,\"ms\":%lf}",
+                         dev, &bc, &P, &K, &F2, &prec, &bucket, &var, &ips, &ms);
+        if (got != 10) continue;
+        if (strcmp(dev, pl->device_name) || bc != pl->bc || P != pl->P || K != pl->K || F2 != pl->F2 ||
+            prec != pl->precision || (var != 2 && var != 4) || ips < 1)
+            continue;
+        bool replaced = false;
+        for (auto &e : pl->tune_entries)
+            if (e.first == bucket) {
+                e.second = hsma_tuning{var, ips, ms};
+                replaced = true;
+            }
+        if (!replaced) pl->tune_entries.push_back({bucket, hsma_tuning{var, ips, ms}});
+        ++loaded;
+    }
+    fclose(f);
+    return loaded;
 }
 
 // -------------------------------------------------------------- direct sums
@@ -1193,7 +1355,7 @@ int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tg
         pa.next_item = ctrl;
         pa.status = status;
         int grid = (int)std::max(1LL, std::min(items, (long long)slots));
-        if ((rc = launch_pair(pa, precision, grid, st))) break;
+        if ((rc = launch_pair(pa, precision, 4, grid, st))) break;
         if ((rc = launch_partial_reduce(dsys, 1, nt, (int)nt, partials, precision, phi, e, st))) break;
         scatter_results_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, phi, e, pot, field);
         HSMA_LAUNCHED();

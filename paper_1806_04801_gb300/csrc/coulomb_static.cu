@@ -224,7 +224,7 @@ extern "C" int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt
     pa.next_item = ctrl;
     pa.status = status;
     const int grid = (int)std::max(1LL, std::min(items, (long long)slots));
-    if ((rc = launch_pair(pa, precision, grid, st))) return rc;
+    if ((rc = launch_pair(pa, precision, 4, grid, st))) return rc;
     if ((rc = launch_partial_reduce(dsys, 1, nt, (int)nt, partials, precision, phi, e, st))) return rc;
     static_scatter_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(nt, phi, e, pot, field);
     HSMA_LAUNCHED();

@@ -26,9 +26,9 @@ namespace hsma {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kT32 = 4;
-constexpr int kTB32 = kThreads * kT32;  // targets per block, FP32 form
-constexpr int kTile32 = 512;            // sources per tile, FP32 form
+// FP32 form: T targets per thread (T = 4 or 2); a block of 128 T targets is
+// exactly one in-set tile of 128 T sources, so a particle block's box is its
+// tile's box.
 constexpr int kT64 = 2;
 constexpr int kTB64 = kThreads * kT64;
 constexpr int kTile64 = 256;
@@ -66,24 +66,24 @@ __device__ __forceinline__ Item decode_item(const PairArgs &a, int item)
 // only: their rounding (<= 2^-24 |x|) then changes each distance by a relative
 // ~1e-6 or less, while the closest pairs -- where an absolute error of
 // ~1e-7 would matter -- always take the split form.
-template <bool FIELD, int SKIP, bool SPLIT>
+template <int T, bool FIELD, int SKIP, bool SPLIT>
 __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int cnt_pad,
-                                       const float (&th)[kT32][3], const float (&tl)[kT32][3],
-                                       const int (&self_rel)[kT32], float2 (&phi)[kT32], float2 (&g)[kT32][3])
+                                       const float (&th)[T][3], const float (&tl)[T][3],
+                                       const int (&self_rel)[T], float2 (&phi)[T], float2 (&g)[T][3])
 {
-    float ga[kT32][3];
+    float ga[T][3];
 #pragma unroll
-    for (int t = 0; t < kT32; ++t) ga[t][0] = ga[t][1] = ga[t][2] = 0.f;
+    for (int t = 0; t < T; ++t) ga[t][0] = ga[t][1] = ga[t][2] = 0.f;
     for (int s0 = 0; s0 < cnt_pad; s0 += kFold) {
-        float pa[kT32];
+        float pa[T];
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) pa[t] = 0.f;
+        for (int t = 0; t < T; ++t) pa[t] = 0.f;
 #pragma unroll 4
         for (int s = 0; s < kFold; ++s) {
             const float4 h = sh[s0 + s];
             const float4 l = SPLIT ? sl[s0 + s] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int t = 0; t < kT32; ++t) {
+            for (int t = 0; t < T; ++t) {
                 float dx, dy, dz;
                 if (SPLIT) {
                     dx = (h.x - th[t][0]) + (l.x - tl[t][0]);
@@ -109,11 +109,11 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
             }
         }
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) phi[t] = df_add(phi[t], pa[t]);
+        for (int t = 0; t < T; ++t) phi[t] = df_add(phi[t], pa[t]);
     }
     if (FIELD) {
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) {
+        for (int t = 0; t < T; ++t) {
             g[t][0] = df_add(g[t][0], ga[t][0]);
             g[t][1] = df_add(g[t][1], ga[t][1]);
             g[t][2] = df_add(g[t][2], ga[t][2]);
@@ -121,11 +121,14 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
+template <int T>
+__global__ void __launch_bounds__(kThreads, (T == 4 ? 4 : 6)) pair_fp32_kernel(PairArgs a)
 {
+    constexpr int TB = kThreads * T;  // targets per block
+    constexpr int TILE = TB;          // sources per tile
     extern __shared__ __align__(128) float4 smem32[];
-    float4 *sh_hi = smem32;                // [2][kTile32]
-    float4 *sh_lo = smem32 + 2 * kTile32;  // [2][kTile32]
+    float4 *sh_hi = smem32;                // [2][TILE]
+    float4 *sh_lo = smem32 + 2 * TILE;  // [2][TILE]
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ int s_item, s_abort;
     const int tid = threadIdx.x;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
         const Item it = decode_item(a, item);
         const SysDesc sd = a.sys[it.sys];
         const long long Ns = a.ns[it.sys];
-        const long long ntiles = (Ns + kTile32 - 1) / kTile32;
+        const long long ntiles = (Ns + TILE - 1) / TILE;
         const int t0 = (int)(it.chunk * ntiles / sd.nchunks);
         const int t1 = (int)((it.chunk + 1) * ntiles / sd.nchunks);
         const bool part = it.tb < sd.ntb_part;
@@ -162,16 +165,16 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
         const long long ntgt = sd.n + a.n_ext;
 
         // targets of this thread
-        float th[kT32][3], tl[kT32][3];
-        long long tidx[kT32];
+        float th[T][3], tl[T][3];
+        long long tidx[T];
         long long tb_lo = 0, tb_hi = 0;  // in-set slots of this block's own particles
         if (part) {
-            tb_lo = (long long)it.tb * kTB32;
-            tb_hi = tb_lo + kTB32;
+            tb_lo = (long long)it.tb * TB;
+            tb_hi = tb_lo + TB;
         }
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) {
-            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * kTB32 + t * kThreads + tid;
+        for (int t = 0; t < T; ++t) {
+            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * TB + t * kThreads + tid;
             bool valid = part ? (k < sd.n) : (k < a.n_ext);
             float4 h = make_float4(kFar, kFar, kFar, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) {
@@ -187,9 +190,9 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
             tl[t][0] = l.x; tl[t][1] = l.y; tl[t][2] = l.z;
             tidx[t] = valid ? (part ? k : sd.n + k) : -1;
         }
-        float2 phi[kT32], g[kT32][3];
+        float2 phi[T], g[T][3];
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) {
+        for (int t = 0; t < T; ++t) {
             phi[t] = make_float2(0.f, 0.f);
             g[t][0] = g[t][1] = g[t][2] = make_float2(0.f, 0.f);
         }
@@ -207,13 +210,13 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
         const float4 *gl = a.src_lo + sd.src_off;
         const int ntile = t1 - t0;
         auto issue = [&](int k, int buf) {
-            long long s0 = (long long)(t0 + k) * kTile32;
-            int cnt = (int)min((long long)kTile32, Ns - s0);
+            long long s0 = (long long)(t0 + k) * TILE;
+            int cnt = (int)min((long long)TILE, Ns - s0);
             uint32_t bytes = (uint32_t)cnt * 16u;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bar[buf], 2u * bytes);
-            bulk_g2s(sh_hi + buf * kTile32, gh + s0, bytes, &bar[buf]);
-            bulk_g2s(sh_lo + buf * kTile32, gl + s0, bytes, &bar[buf]);
+            bulk_g2s(sh_hi + buf * TILE, gh + s0, bytes, &bar[buf]);
+            bulk_g2s(sh_lo + buf * TILE, gl + s0, bytes, &bar[buf]);
         };
         if (tid == 0) {
             if (ntile > 0) issue(0, 0);
@@ -226,11 +229,11 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
                 atomicOr(&a.status[it.sys], ST_TIMEOUT);
             }
             parity[buf] ^= 1u;
-            const long long s0 = (long long)(t0 + k) * kTile32;
-            const int cnt = (int)min((long long)kTile32, Ns - s0);
+            const long long s0 = (long long)(t0 + k) * TILE;
+            const int cnt = (int)min((long long)TILE, Ns - s0);
             const int cnt_pad = (cnt + kFold - 1) / kFold * kFold;
-            float4 *bh = sh_hi + buf * kTile32;
-            float4 *bl = sh_lo + buf * kTile32;
+            float4 *bh = sh_hi + buf * TILE;
+            float4 *bl = sh_lo + buf * TILE;
             if (cnt_pad > cnt) {
                 for (int s = cnt + tid; s < cnt_pad; s += kThreads) {
                     bh[s] = make_float4(kFar, -kFar, kFar, 0.f);
@@ -240,9 +243,9 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
             __syncthreads();
             if (s_abort) break;
             const int skip = part ? ((s0 < tb_hi && s0 + cnt > tb_lo) ? 1 : 0) : (a.ext_skip_zero ? 2 : 0);
-            int self_rel[kT32];
+            int self_rel[T];
 #pragma unroll
-            for (int t = 0; t < kT32; ++t) self_rel[t] = (int)(tidx[t] - s0);
+            for (int t = 0; t < T; ++t) self_rel[t] = (int)(tidx[t] - s0);
             bool far = false;
             if (use_boxes && skip == 0) {
                 const float4 slo = a.boxes[2 * (sd.tile_off + t0 + k)];
@@ -254,20 +257,20 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
             }
             if (field) {
                 if (far)
-                    tile32<true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 1)
-                    tile32<true, 1, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, true, 1, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 2)
-                    tile32<true, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, true, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             } else {
                 if (far)
-                    tile32<false, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, false, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 2)
-                    tile32<false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             }
             __syncthreads();
             if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp32_kernel(PairArgs a)
         }
         float4 *rec = a.partials + 2 * (sd.partial_off + (long long)it.chunk * ntgt);
 #pragma unroll
-        for (int t = 0; t < kT32; ++t) {
+        for (int t = 0; t < T; ++t) {
             if (tidx[t] < 0) continue;
             rec[2 * tidx[t]] = make_float4(phi[t].x, phi[t].y, g[t][0].x, g[t][0].y);
             rec[2 * tidx[t] + 1] = make_float4(g[t][1].x, g[t][1].y, g[t][2].x, g[t][2].y);
@@ -467,38 +470,46 @@ __global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float
 
 }  // namespace
 
-int pair_targets_per_block(int precision) { return precision == HSMA_FP64 ? kTB64 : kTB32; }
-
-static size_t pair_smem(int precision)
+int pair_targets_per_block(int precision, int variant)
 {
-    return precision == HSMA_FP64 ? 2 * kTile64 * sizeof(double4_32a) : 4 * kTile32 * sizeof(float4);
+    return precision == HSMA_FP64 ? kTB64 : kThreads * (variant == 2 ? 2 : 4);
 }
 
-int pair_max_ctas_per_sm(int precision)
+static size_t pair_smem(int precision, int variant)
+{
+    return precision == HSMA_FP64 ? 2 * kTile64 * sizeof(double4_32a)
+                                  : 4 * (size_t)pair_targets_per_block(precision, variant) * sizeof(float4);
+}
+
+template <class K>
+static int occupancy_of(K kernel, size_t sm)
 {
     int n = 0;
-    size_t sm = pair_smem(precision);
-    if (precision == HSMA_FP64) {
-        cudaFuncSetAttribute(pair_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp64_kernel, kThreads, sm);
-    } else {
-        cudaFuncSetAttribute(pair_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_fp32_kernel, kThreads, sm);
-    }
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, sm);
     return n > 0 ? n : 1;
+}
+
+int pair_max_ctas_per_sm(int precision, int variant)
+{
+    const size_t sm = pair_smem(precision, variant);
+    if (precision == HSMA_FP64) return occupancy_of(pair_fp64_kernel, sm);
+    return variant == 2 ? occupancy_of(pair_fp32_kernel<2>, sm) : occupancy_of(pair_fp32_kernel<4>, sm);
 }
 
 // The dynamic shared-memory attribute is set by pair_max_ctas_per_sm, which
 // every caller runs before its first launch (so that launches can be
 // captured into a CUDA graph).
-int launch_pair(const PairArgs &a, int precision, int grid, cudaStream_t st)
+int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStream_t st)
 {
     if (a.total_items <= 0) return HSMA_OK;
-    size_t sm = pair_smem(precision);
+    const size_t sm = pair_smem(precision, variant);
     if (precision == HSMA_FP64)
         pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
+    else if (variant == 2)
+        pair_fp32_kernel<2><<<grid, kThreads, sm, st>>>(a);
     else
-        pair_fp32_kernel<<<grid, kThreads, sm, st>>>(a);
+        pair_fp32_kernel<4><<<grid, kThreads, sm, st>>>(a);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

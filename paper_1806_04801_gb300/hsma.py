@@ -44,6 +44,10 @@ class hsma_out(ctypes.Structure):
                 ("n_inset", ctypes.c_int64), ("n_images", ctypes.c_int)]
 
 
+class hsma_tuning(ctypes.Structure):
+    _fields_ = [("pair_variant", ctypes.c_int), ("items_per_slot", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
 class hsma_plan_info_t(ctypes.Structure):
     _fields_ = [("bc", ctypes.c_int), ("p", ctypes.c_int), ("n_basis", ctypes.c_int), ("n_cols", ctypes.c_int),
                 ("Kmon", ctypes.c_int), ("n_mon_targets", ctypes.c_int), ("F2", ctypes.c_int),
@@ -74,6 +78,11 @@ SIGNATURES = {
     "hsma_kernel_launches": (_I64, []),
     "hsma_last_timings": (_I, [_VP, _VP, _I]),
     "hsma_last_get": (_I64, [_VP, _I, _VP, _I64]),
+    "hsma_plan_set_tuning": (_I, [_VP, ctypes.POINTER(hsma_tuning)]),
+    "hsma_plan_get_tuning": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_tuning)]),
+    "hsma_autotune": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_particles), ctypes.c_char_p,
+                           ctypes.POINTER(hsma_tuning)]),
+    "hsma_plan_load_tuning": (_I, [_VP, ctypes.c_char_p]),
 }
 
 _LIB = None
@@ -264,6 +273,40 @@ class Plan:
                                                _ptr_and_dev(p)[0] if p is not None else None, st.ctypes.data)
         _check(rc, "hsma_energy_forces_batched")
         return e, f, p, st
+
+    # ------------------------------------------------------------ tuning
+    def set_tuning(self, pair_variant=None, items_per_slot=None):
+        """Fix the pair kernel's work decomposition (None, None: automatic)."""
+        if pair_variant is None and items_per_slot is None:
+            _check(_lib().hsma_plan_set_tuning(self._h, None), "hsma_plan_set_tuning")
+            return
+        t = hsma_tuning(int(pair_variant or 4), int(items_per_slot or 24), 0.0)
+        _check(_lib().hsma_plan_set_tuning(self._h, ctypes.byref(t)), "hsma_plan_set_tuning")
+
+    def get_tuning(self, offsets) -> dict:
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        t = hsma_tuning()
+        _check(_lib().hsma_plan_get_tuning(self._h, off.shape[0] - 1, off.ctypes.data, ctypes.byref(t)),
+               "hsma_plan_get_tuning")
+        return {"pair_variant": t.pair_variant, "items_per_slot": t.items_per_slot, "ms": t.ms}
+
+    def autotune(self, xyz, q, offsets=None, cache_path=None) -> dict:
+        """hsma_autotune on a batch (offsets None: one system)."""
+        pxyz, dev = _ptr_and_dev(xyz)
+        pq, _ = _ptr_and_dev(q)
+        n = int(q.shape[0])
+        off = np.ascontiguousarray([0, n] if offsets is None else offsets, dtype=np.int64)
+        part = hsma_particles(n, pxyz, pq, 1 if dev else 0)
+        t = hsma_tuning()
+        _check(_lib().hsma_autotune(self._h, off.shape[0] - 1, off.ctypes.data, ctypes.byref(part),
+                                    cache_path.encode() if cache_path else None, ctypes.byref(t)), "hsma_autotune")
+        return {"pair_variant": t.pair_variant, "items_per_slot": t.items_per_slot, "ms": t.ms}
+
+    def load_tuning(self, cache_path) -> int:
+        r = _lib().hsma_plan_load_tuning(self._h, str(cache_path).encode())
+        if r < 0:
+            raise HsmaError(r, "hsma_plan_load_tuning")
+        return int(r)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -154,3 +154,42 @@ def test_serving_rejects_requests_beyond_budget():
         assert code_s == 0 and np.isfinite(E)
         # a ticket is collected once
         assert srv.result(ts, n=1)[0] == -9
+
+
+def test_autotuner_and_both_kernel_variants(tmp_path):
+    """Both work decompositions of the pair kernel give the same physics (to
+    FP32 rounding); the autotuner picks one, records it, and a new plan loads
+    it back from the cache."""
+    w = I.BATCH_PERIODIC
+    systems = [I.uniform_pm1(int(n), w.box, seed_offset=90 + i) for i, n in enumerate([600, 3000, 9000, 1200])]
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    dx, dq = to_dev(xyz, q)
+    res = {}
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        for var in (4, 2):
+            for ips in (8, 48):
+                plan.set_tuning(var, ips)
+                E, F, _, st = plan.energy_forces_batched(dx, dq, off)
+                assert np.all(st == 0)
+                res[(var, ips)] = (E, F.cpu().numpy())
+        E0, F0 = res[(4, 8)]
+        for k, (E, F) in res.items():
+            for i in range(len(systems)):
+                sl = slice(off[i], off[i + 1])
+                assert rel_energy_err(E[i], E0[i], systems[i][1]) <= 1e-6, k
+                assert rms(F[sl] - F0[sl]) <= 1e-5 * rms(F0[sl]), k
+        plan.set_tuning(None, None)
+        cache = str(tmp_path / "tune.jsonl")
+        best = plan.autotune(dx, dq, off, cache_path=cache)
+        assert best["pair_variant"] in (2, 4) and best["items_per_slot"] in (8, 16, 24, 48) and best["ms"] > 0
+        assert plan.get_tuning(off)["pair_variant"] == best["pair_variant"]
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan2:
+        assert plan2.get_tuning(off)["items_per_slot"] == 24  # defaults before loading
+        assert plan2.load_tuning(cache) == 1
+        t2 = plan2.get_tuning(off)
+        assert (t2["pair_variant"], t2["items_per_slot"]) == (best["pair_variant"], best["items_per_slot"])
+        E, F, _, _ = plan2.energy_forces_batched(dx, dq, off)
+        for i in range(len(systems)):
+            assert rel_energy_err(E[i], E0[i], systems[i][1]) <= 1e-6

@@ -82,7 +82,11 @@ typedef struct {
     int fib_F2;         /* > 0: Fibonacci number F2 of the surface quadrature;
                            0: chosen from Q as the F2 whose 6(F2+1) is nearest
                            to Q (ties to the larger)                         */
-    int reserved0;      /* must be 0                                         */
+    int far_field;      /* how Phi_out reaches the particles: 0 = the point
+                           and dipole images on the auxiliary sphere (Sec.
+                           II.B, the paper's method); 1 = direct evaluation
+                           of the fitted series sum A_nm B_nm(r) and its
+                           gradient at each particle (FP64)                 */
     void *stream;       /* cudaStream_t for all device work; NULL = default  */
     int use_graphs;     /* 1 = capture the update step in a CUDA graph (default) */
     int profile;        /* 1 = record per-phase CUDA-event timings           */

@@ -222,3 +222,37 @@ def error_bound_potential(alpha, P, Rs, d0, qmax):
 def error_bound_gradient(alpha, P, Rs, d0, qmax):
     """Truncation bound on each gradient component (Sec. II.A and Appendix)."""
     return 4 * math.pi * d0 * Rs * qmax / ((alpha - 1) * (P - 2)) * (P + alpha / (alpha - 1)) * alpha ** (-(P - 1))
+
+
+def series_far_field(plan: Plan, A, pts, h: float = 1e-4):
+    """Phi_out = sum_k A_k B_k(r) evaluated directly at points (Eq.
+    "harmonic"), and E_out = -grad Phi_out by fourth-order central
+    differences with step h (relative to Rs).  The alternative to the
+    surface images of Sec. II.B for bringing the fitted far field to the
+    particles."""
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
+    phi = basis(pts, plan.P, plan.Rs) @ A
+    step = h * plan.Rs
+    field = np.empty_like(pts)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = step
+        f = lambda d: basis(pts + d * e, plan.P, plan.Rs) @ A  # noqa: E731
+        deriv = (-f(2) + 8 * f(1) - 8 * f(-1) + f(-2)) / (12 * step)
+        field[:, a] = -deriv
+    return phi, field
+
+
+def energy_forces_series(xyz, q, plan: Plan, nthreads: int = 1) -> dict:
+    """The update step with the far field evaluated as the fitted series at
+    each particle instead of through surface images (same in-set, fit and
+    energy/force definitions as energy_forces)."""
+    out = energy_forces(xyz, q, plan, nthreads=nthreads)
+    c = centre_positions(xyz, plan.box, plan.bc)
+    phi_s, e_s = series_far_field(plan, out["A"], c)
+    q = np.asarray(q, dtype=np.float64)
+    pot = out["phi_in"] + phi_s
+    res = dict(out)
+    res.update(pot=pot, phi_out=phi_s, e_out=e_s, forces=q[:, None] * (out["e_in"] + e_s),
+               energy=0.5 * float(np.dot(q, pot)))
+    return res

@@ -93,6 +93,7 @@ struct hsma_plan_s {
     double Rs, R0, dr, alpha, cond;
     double far_rel = 1.0 / 15.0;  // near/far threshold of the FP32 pair sums, in units of Rs
     int stall_test = 0;           // HSMA_TEST_STALL_WAIT=1 at plan creation: exercise the timeout path
+    int far_field = 0;            // 0: surface images (Sec. II.B); 1: direct series at the particles
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
     int num_sms, ctas[3], ctas_v2;
@@ -497,13 +498,22 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     if (rc) return rc;
     record(p, st, 4);
 
-    // (d) surface images and their sums at the particles
-    if ((rc = launch_surface_charges(nsys, p->ndir, p->Nb, p->Bq, p->dirs, w.A, p->Rs, w.img, st))) return rc;
-    record(p, st, 5);
-    if ((rc = launch_surface_pairs(w.sys, nsys, sh.surf_items, w.ns, w.src_hi, w.src_lo, w.src64, p->ndir, p->dirs,
-                                   w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st)))
-        return rc;
-    record(p, st, 6);
+    if (p->far_field == 1) {
+        // far field by the fitted series evaluated at each particle
+        record(p, st, 5);
+        if ((rc = launch_series_field(w.sys, nsys, sh.max_n, p->P, p->Rs, p->norm, w.A, w.src_hi, w.src_lo, w.src64,
+                                      w.phi_out, w.e_out, st)))
+            return rc;
+        record(p, st, 6);
+    } else {
+        // (d) surface images and their sums at the particles
+        if ((rc = launch_surface_charges(nsys, p->ndir, p->Nb, p->Bq, p->dirs, w.A, p->Rs, w.img, st))) return rc;
+        record(p, st, 5);
+        if ((rc = launch_surface_pairs(w.sys, nsys, sh.surf_items, w.ns, w.src_hi, w.src_lo, w.src64, p->ndir,
+                                       p->dirs, w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st)))
+            return rc;
+        record(p, st, 6);
+    }
     if ((rc = launch_finalize(w.sys, nsys, sh.max_n, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
                               want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, w.upart, w.energy, w.status,
                               st)))
@@ -723,7 +733,7 @@ int hsma_opts_default(hsma_opts *o)
     o->precision = HSMA_FP32_ACC64;
     o->dr_rel = 0.0;
     o->fib_F2 = 0;
-    o->reserved0 = 0;
+    o->far_field = 0;
     o->stream = nullptr;
     o->use_graphs = 1;
     o->profile = 0;
@@ -799,6 +809,11 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     pl->use_graphs = o.use_graphs;
     pl->profile = o.profile;
     pl->stream = (cudaStream_t)o.stream;
+    if (o.far_field != 0 && o.far_field != 1) {
+        delete pl;
+        return HSMA_E_ARG;
+    }
+    pl->far_field = o.far_field;
     {
         const char *e = getenv("HSMA_TEST_STALL_WAIT");
         pl->stall_test = (e && e[0] == '1') ? 1 : 0;

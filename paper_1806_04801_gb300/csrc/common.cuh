@@ -272,6 +272,9 @@ int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const lo
                          const float4 *src_lo, const double4_32a *src64, int ndir, const double4_32a *dirs,
                          const double2 *img, double Rs, double dr, int precision, double *phi_out,
                          double *e_out, cudaStream_t st);
+int launch_series_field(const SysDesc *sys, int nsys, long long max_n, int P, double Rs, const double *norm,
+                        const double *A, const float4 *src_hi, const float4 *src_lo, const double4_32a *src64,
+                        double *phi_out, double *e_out, cudaStream_t st);
 int finalize_blocks(long long max_n);
 int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *perm, const double *q,
                     const double *phi_tgt, const double *e_part, const double *phi_out, const double *e_out,

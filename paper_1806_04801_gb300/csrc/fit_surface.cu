@@ -382,3 +382,111 @@ int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *pe
 }
 
 }  // namespace hsma
+
+namespace hsma {
+
+namespace {
+
+// Direct evaluation of the far field at the particles: Phi_out(r) =
+// sum_k A_k B_k(r) (Eq. "harmonic") and E_out = -grad Phi_out, in FP64.  The
+// basis is the orthonormal real solid harmonics of basis_kernel:
+//   B = norm_k * Pi_n^m(z, r2) * Re/Im (x + i y)^m   (coordinates / Rs),
+// with Pi from its three-term recurrence; the recurrence is differentiated
+// alongside for dPi/dz and dPi/d(r2), so that
+//   grad B = norm_k [ Pi grad(C_m|S_m) + (C_m|S_m)(dPi/dz e_z + 2 dPi/d(r2) r) ],
+//   d/dx (C_m + i S_m) = m (C_{m-1} + i S_{m-1}),
+//   d/dy (C_m + i S_m) = i m (C_{m-1} + i S_{m-1}).
+__global__ void series_field_kernel(const SysDesc *sys, int nsys, int P, double inv_rs, const double *norm,
+                                    const double *A, const float4 *src_hi, const float4 *src_lo,
+                                    const double4_32a *src64, double *phi_out, double *e_out)
+{
+    const int s = blockIdx.y;
+    const SysDesc sd = sys[s];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sd.n) return;
+    double x, y, z;
+    if (src64) {
+        double4_32a p = src64[sd.src_off + i];
+        x = p.x; y = p.y; z = p.z;
+    } else {
+        float4 h = src_hi[sd.src_off + i], l = src_lo[sd.src_off + i];
+        x = (double)h.x + (double)l.x;
+        y = (double)h.y + (double)l.y;
+        z = (double)h.z + (double)l.z;
+    }
+    x *= inv_rs; y *= inv_rs; z *= inv_rs;
+    const double r2 = x * x + y * y + z * z;
+    const int Nb = (P + 1) * (P + 1);
+    const double *a = A + (long long)s * Nb;
+    double phi = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    double cm = 1.0, sm = 0.0, cp = 0.0, sp = 0.0;  // (x+iy)^m and (x+iy)^(m-1)
+    double pmm = 1.0;
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            cp = cm;
+            sp = sm;
+            double c2 = cm * x - sm * y;
+            sm = sm * x + cm * y;
+            cm = c2;
+            pmm *= (2.0 * m - 1.0);
+        }
+        // Pi_{n-1}, Pi_{n-2} and their z / r2 derivatives
+        double p1 = 0, p2 = 0, z1 = 0, z2 = 0, q1 = 0, q2 = 0;
+        for (int n = m; n <= P; ++n) {
+            double pn, dz, dq;
+            if (n == m) {
+                pn = pmm; dz = 0.0; dq = 0.0;
+            } else if (n == m + 1) {
+                pn = (2.0 * m + 1.0) * z * pmm;
+                dz = (2.0 * m + 1.0) * pmm;
+                dq = 0.0;
+            } else {
+                const double inv = 1.0 / (double)(n - m);
+                pn = ((2.0 * n - 1.0) * z * p1 - (n + m - 1.0) * r2 * p2) * inv;
+                dz = ((2.0 * n - 1.0) * (p1 + z * z1) - (n + m - 1.0) * r2 * z2) * inv;
+                dq = ((2.0 * n - 1.0) * z * q1 - (n + m - 1.0) * (p2 + r2 * q2)) * inv;
+            }
+            p2 = p1; p1 = pn;
+            z2 = z1; z1 = dz;
+            q2 = q1; q1 = dq;
+            // radial part gradient: dPi/dz e_z + 2 dPi/dr2 (x, y, z)
+            const double rx = 2.0 * dq * x, ry = 2.0 * dq * y, rz = dz + 2.0 * dq * z;
+            const int kc = n * n + n + m;
+            const double ac = a[kc] * norm[kc];
+            phi += ac * pn * cm;
+            gx += ac * (pn * m * cp + cm * rx);
+            gy += ac * (-pn * m * sp + cm * ry);
+            gz += ac * (cm * rz);
+            if (m > 0) {
+                const int ks = n * n + n - m;
+                const double as = a[ks] * norm[ks];
+                phi += as * pn * sm;
+                gx += as * (pn * m * sp + sm * rx);
+                gy += as * (pn * m * cp + sm * ry);
+                gz += as * (sm * rz);
+            }
+        }
+    }
+    const long long o = sd.part_off + i;
+    phi_out[o] = phi;
+    // gradient w.r.t. the scaled coordinates -> physical: times 1/Rs; E = -grad
+    e_out[3 * o] = -gx * inv_rs;
+    e_out[3 * o + 1] = -gy * inv_rs;
+    e_out[3 * o + 2] = -gz * inv_rs;
+}
+
+}  // namespace
+
+int launch_series_field(const SysDesc *sys, int nsys, long long max_n, int P, double Rs, const double *norm,
+                        const double *A, const float4 *src_hi, const float4 *src_lo, const double4_32a *src64,
+                        double *phi_out, double *e_out, cudaStream_t st)
+{
+    dim3 grid((unsigned)((max_n + 127) / 128), nsys);
+    series_field_kernel<<<grid, 128, 0, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, src64, phi_out,
+                                              e_out);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+}  // namespace hsma

@@ -30,7 +30,7 @@ class HsmaError(RuntimeError):
 
 class hsma_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("dr_rel", ctypes.c_double), ("fib_F2", ctypes.c_int),
-                ("reserved0", ctypes.c_int), ("stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
+                ("far_field", ctypes.c_int), ("stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
                 ("profile", ctypes.c_int)]
 
 
@@ -151,7 +151,8 @@ class Plan:
     """hsma_plan: preparation step; device-resident matrices."""
 
     def __init__(self, box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64,
-                 dr_rel: float = 0.0, fib_F2: int = 0, stream=None, profile: bool = False, use_graphs: bool = True):
+                 dr_rel: float = 0.0, fib_F2: int = 0, stream=None, profile: bool = False, use_graphs: bool = True,
+                 far_field: str = "images"):
         L = _lib()
         o = hsma_opts()
         _check(L.hsma_opts_default(ctypes.byref(o)), "hsma_opts_default")
@@ -161,6 +162,7 @@ class Plan:
         o.stream = _stream_handle(stream)
         o.profile = 1 if profile else 0
         o.use_graphs = 1 if use_graphs else 0
+        o.far_field = {"images": 0, "series": 1}[far_field]
         box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
         h = ctypes.c_void_p()
         _check(L.hsma_plan(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon), ctypes.byref(o)),

@@ -306,3 +306,34 @@ def test_large_periodic_fp64_full_energy():
     with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
         U32, F32, _, _ = plan.energy_forces(*to_dev(xyz, q))
     assert_within(errors(F32.cpu().numpy(), ref["forces"], U32, ref["energy"]), "fp32", "periodic 1e5 full")
+
+
+@pytest.mark.parametrize("bc", ["periodic", "grounded"])
+def test_series_far_field(bc):
+    """Far field by the fitted series at each particle (far_field = series):
+    against the oracle's series evaluation (its field by central differences,
+    accurate to ~1e-9) and against the GPU's own surface-image path."""
+    from oracle import hsma as oh
+    if bc == "periodic":
+        w = I.SMALL_PERIODIC
+        xyz, q = I.small_periodic()
+    else:
+        w = I.Workload("grounded-small", (1.0, 1.0, 2.0), I.GROUNDED, 10, I.GROUNDED_CAVITY.R, 6000, 1500)
+        xyz, q = I.uniform_pm1(1500, w.box, seed_offset=20, margin=0.05)
+    F2, _ = oh.fib_from_points(w.Q)
+    oplan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
+    ref = oh.energy_forces_series(xyz, q, oplan, nthreads=8)
+    dx, dq = to_dev(xyz, q)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64", far_field="series") as plan:
+        U, F, pot, _ = plan.energy_forces(dx, dq, potentials=True)
+        e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+        assert e["energy"] <= 1e-10 and e["pot_rms"] <= 1e-10 and e["force_rms"] <= 1e-8, e
+        phi_out = plan.last_get(4, len(q))
+        assert rms(phi_out - ref["phi_out"]) <= 1e-10 * rms(ref["phi_out"])
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", far_field="series") as plan:
+        U32, F32, _, _ = plan.energy_forces(dx, dq)
+        assert_within(errors(F32.cpu().numpy(), ref["forces"], U32, ref["energy"]), "fp32", "series fp32")
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as plan:
+        Ui, Fi, _, _ = plan.energy_forces(dx, dq)
+    # mapping accuracy of the surface images (quadrature + O(dr^2))
+    assert abs(Ui - U) <= 1e-7 * abs(U)

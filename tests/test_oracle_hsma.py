@@ -171,3 +171,21 @@ def test_nonneutral_periodic_rejected():
     plan = _plan_for_mapping(P=4, F2=89)
     with pytest.raises(ValueError):
         hsma.energy_forces(np.full((2, 3), 0.3), np.array([1.0, 0.5]), plan)
+
+
+def test_series_far_field_matches_surface_images():
+    # the two ways of bringing the fitted far field to the particles agree to
+    # the mapping accuracy (quadrature + O(dr^2)), and the series' field is
+    # minus the gradient of its potential
+    L = np.ones(3)
+    xyz, q = inputs.random_neutral(24, L, 33)
+    Rs = hsma.alpha_to_rs(L, 2.0)
+    plan = hsma.make_plan(L, hsma.PERIODIC, 14, Rs, 2 * 14 * 14, 987)
+    img = hsma.energy_forces(xyz, q, plan)
+    ser = hsma.energy_forces_series(xyz, q, plan)
+    assert abs(ser["energy"] - img["energy"]) <= 1e-9 * abs(img["energy"])
+    np.testing.assert_allclose(ser["phi_out"], img["phi_out"], rtol=0, atol=1e-9 * np.abs(img["phi_out"]).max())
+    np.testing.assert_allclose(ser["e_out"], img["e_out"], rtol=0, atol=1e-7 * np.abs(img["e_out"]).max())
+    # both against Ewald
+    _, fld, U = checks.ewald_periodic(xyz, q, L)
+    assert abs(ser["energy"] - U) <= 1e-7 * abs(U)

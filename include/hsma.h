@@ -187,6 +187,34 @@ int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offset
                                const hsma_particles *all, double *energies, double *forces,
                                double *potentials, int *status);
 
+/* ------------------------------------------------------- target sharding */
+/* The update step split so that one system can be shared by several GPUs
+ * (one process per GPU, each with a plan of the same parameters and all n
+ * particles).  Part `part` of `nparts` owns a contiguous slice of the
+ * particles in the plan's spatial (Morton) order -- whole blocks of the pair
+ * kernel -- and a slice of the monitoring targets.
+ *
+ *   1. hsma_shard_near: Phi_in and E_in at the owned particles (Sec. II.A
+ *      near-field sums over the whole in-set), and Phi_in at the owned
+ *      monitoring targets, written into phi_mon (host, n_mon_targets, in the
+ *      order of hsma_plan_get_matrix(0); zero outside the owned slice).
+ *   2. The caller sums phi_mon over the parts (an all-reduce, or all-gather,
+ *      of n_mon_targets doubles).
+ *   3. hsma_shard_far: the fit from the full phi_mon (the same on every
+ *      part), the surface images (or series) and Phi_out, E_out at the owned
+ *      particles.
+ *   4. The caller forms U = 1/2 sum q_i (phi_in + phi_out) over its particles
+ *      and all-reduces it; F_i = q_i (E_in + E_out).
+ *
+ * Outputs are host arrays of capacity n: index[j] is the caller's index of
+ * the j-th owned particle, phi[j] and field[3j..3j+2] its values; *count
+ * receives the number of owned particles (the same slice in both stages).
+ * x_q may be host or device.  Errors as hsma_energy_forces. */
+int hsma_shard_near(hsma_plan_t plan, const hsma_particles *x_q, int part, int nparts, int64_t *index,
+                    double *phi, double *field, int64_t *count, double *phi_mon);
+int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *phi_mon, int part, int nparts,
+                   int64_t *index, double *phi, double *field, int64_t *count);
+
 /* ----------------------------------------------------------------- tuning */
 /* Work decomposition of the near-field pair kernel (no counterpart in the
  * paper; it changes speed, not results beyond rounding of the chunk

@@ -73,6 +73,7 @@ struct Workspace {
     int *ctrl = nullptr;                            // work counters
     SysDesc *sys = nullptr;
     float *tc_work = nullptr;
+    long long *idx64 = nullptr;                     // target sharding: caller indices of a slice
 };
 
 struct BatchShape {
@@ -288,6 +289,10 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         d.partial_off = rec;
         d.item_off = (int)items;
         d.surf_off = (int)surf;
+        d.sp_lo = 0;
+        d.sp_n = n[s];
+        d.pb_lo = 0;
+        d.mb_lo = 0;
         long long ntgt = n[s] + p->nmon;
         part += n[s];
         src += n[s] * p->nshifts;
@@ -357,6 +362,7 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     w->sys = c.take<SysDesc>(sh.nsys);
     w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys))
                                                   : nullptr;
+    w->idx64 = c.take<long long>(sh.n_total);
     return align_up(c.off, 256);
 }
 
@@ -701,6 +707,184 @@ int sort_monitor_targets(hsma_plan_s *p, cudaStream_t st)
     if (rc) return rc;
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above go out of scope
     return HSMA_OK;
+}
+
+__global__ void shard_gather_kernel(long long lo, long long cnt, const int *perm, const double *phi_src,
+                                    const double *e_src, long long *idx_out, double *phi_out, double *field_out)
+{
+    long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt) return;
+    long long i = lo + j;
+    idx_out[j] = perm[i];
+    phi_out[j] = phi_src[i];
+    field_out[3 * j] = e_src[3 * i];
+    field_out[3 * j + 1] = e_src[3 * i + 1];
+    field_out[3 * j + 2] = e_src[3 * i + 2];
+}
+
+// One stage of the target-sharded update step for part `part` of `nparts`
+// (see hsma_shard_near / hsma_shard_far).  Single system; host outputs.
+int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part, int nparts,
+              const double *phi_mon_in, double *phi_mon_out, int64_t *index, double *phi, double *field,
+              int64_t *count)
+{
+    if (!p || !x || !x->xyz || !x->q || x->n < 1 || nparts < 1 || part < 0 || part >= nparts || !index || !phi ||
+        !field || !count)
+        return HSMA_E_ARG;
+    if (far_stage ? !phi_mon_in : !phi_mon_out) return HSMA_E_ARG;
+    const long long n = x->n;
+    const int prec = p->precision;
+    BatchShape sh;
+    shape_batch(p, 1, &n, prec, choose_tuning(p, 1, &n), &sh);
+    SysDesc &d = sh.sys[0];
+    const int TB = pair_targets_per_block(prec, sh.variant);
+    const int STB = surface_targets_per_block();
+    const long long nb = (n + TB - 1) / TB, nbm = (p->nmon + TB - 1) / TB;
+    const int pb_lo = (int)(part * nb / nparts), pb_hi = (int)((part + 1) * nb / nparts);
+    const int mb_lo = (int)(part * nbm / nparts), mb_hi = (int)((part + 1) * nbm / nparts);
+    const long long t_lo = std::min<long long>((long long)pb_lo * TB, n);
+    const long long t_hi = std::min<long long>((long long)pb_hi * TB, n);
+    const long long m_lo = std::min<long long>((long long)mb_lo * TB, p->nmon);
+    const long long m_hi = std::min<long long>((long long)mb_hi * TB, p->nmon);
+    d.pb_lo = pb_lo;
+    d.mb_lo = mb_lo;
+    d.ntb_part = pb_hi - pb_lo;
+    d.ntb = d.ntb_part + (mb_hi - mb_lo);
+    sh.items = d.ntb * d.nchunks;
+    d.sp_lo = t_lo;
+    d.sp_n = t_hi - t_lo;
+    sh.surf_items = (int)((d.sp_n + STB - 1) / STB);
+
+    Workspace w;
+    size_t need = carve_workspace(p, sh, prec, true, true, nullptr, &w);
+    int rc = ensure_workspace(p, need);
+    if (rc) return rc;
+    carve_workspace(p, sh, prec, true, true, p->ws_mem, &w);
+    p->ws = w;
+    if ((rc = ensure_pinned(p, sizeof(SysDesc) + 64))) return rc;
+    memcpy(p->hpin, &d, sizeof(SysDesc));
+    cudaStream_t st;
+    if ((rc = work_stream(p, &st))) return rc;
+    const cudaMemcpyKind in_kind = x->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.sys, p->hpin, sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.xyz, x->xyz, sizeof(double) * 3 * n, in_kind, st));
+    HSMA_CUDA_TRY(cudaMemcpyAsync(w.q, x->q, sizeof(double) * n, in_kind, st));
+    HSMA_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    HSMA_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
+
+    // sort and in-set (both stages: the far stage needs the particles in
+    // spatial order again)
+    SortArgs sa;
+    sa.sys = w.sys;
+    sa.nsys = 1;
+    sa.xyz = w.xyz;
+    for (int a = 0; a < 3; ++a) sa.g.L[a] = p->L[a];
+    sa.g.Rs = p->Rs;
+    sa.g.bc = p->bc;
+    sa.keys = w.keys;
+    sa.vals = w.perm;
+    sa.keys2 = w.keys2;
+    sa.vals2 = w.vals2;
+    sa.hist = w.hist;
+    if ((rc = launch_sort_particles(sa, sh.nblk_max, st))) return rc;
+    InsetArgs ia;
+    ia.sys = w.sys;
+    ia.nsys = 1;
+    ia.nblk_max = sh.nblk_max;
+    ia.xyz = w.xyz;
+    ia.q = w.q;
+    ia.perm = w.perm;
+    ia.shifts = p->shifts;
+    ia.n_shifts = p->nshifts;
+    ia.g = sa.g;
+    ia.counts = w.counts;
+    ia.ns = w.ns;
+    ia.src_hi = w.src_hi;
+    ia.src_lo = w.src_lo;
+    ia.src64 = w.src64;
+    ia.status = w.status;
+    if ((rc = launch_inset(ia, st))) return rc;
+
+    const long long cnt = t_hi - t_lo;
+    std::vector<double> mon(p->nmon);
+    if (!far_stage) {
+        if (w.boxes && (rc = launch_tile_boxes(w.sys, 1, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
+        PairArgs pa;
+        pa.sys = w.sys;
+        pa.nsys = 1;
+        pa.total_items = sh.items;
+        pa.ns = w.ns;
+        pa.src_hi = w.src_hi;
+        pa.src_lo = w.src_lo;
+        pa.src64 = w.src64;
+        pa.ext_hi = p->mon_hi_s;
+        pa.ext_lo = p->mon_lo_s;
+        pa.ext64 = p->mon64_s;
+        pa.n_ext = p->nmon;
+        pa.ext_field = 0;
+        pa.ext_skip_zero = 0;
+        pa.boxes = w.boxes;
+        pa.ext_boxes = w.boxes ? (sh.variant == 2 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
+        pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
+        pa.partials = w.partials;
+        pa.next_item = w.ctrl;
+        pa.status = w.status;
+        const int grid = std::max(1, std::min(sh.items, p->num_sms * tuned_ctas(p, prec, sh.variant)));
+        if ((rc = launch_pair(pa, prec, sh.variant, grid, st))) return rc;
+        if ((rc = launch_partial_reduce(w.sys, 1, sh.max_tgt, p->nmon, w.partials, prec, w.phi_tgt, w.e_part, st)))
+            return rc;
+        if (cnt > 0) {
+            shard_gather_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(t_lo, cnt, w.perm, w.phi_tgt,
+                                                                                w.e_part, w.idx64, w.pot, w.forces);
+            HSMA_LAUNCHED();
+        }
+        HSMA_CUDA_TRY(cudaMemcpyAsync(mon.data(), w.phi_tgt + n, sizeof(double) * p->nmon, cudaMemcpyDeviceToHost,
+                                      st));
+    } else {
+        // the full monitoring potentials, into the spatially ordered slots
+        for (int k = 0; k < p->nmon; ++k) mon[k] = phi_mon_in[p->mon_perm[k]];
+        HSMA_CUDA_TRY(cudaMemcpyAsync(w.phi_tgt + n, mon.data(), sizeof(double) * p->nmon, cudaMemcpyHostToDevice,
+                                      st));
+        if (prec == HSMA_FP32_TC_FIT)
+            rc = launch_fit_tc(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
+                               p->mon_inv, w.b, w.A, w.tc_work, st);
+        else
+            rc = launch_fit_fp64(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A, st);
+        if (rc) return rc;
+        if (p->far_field == 1) {
+            rc = launch_series_field(w.sys, 1, std::max<long long>(cnt, 1), p->P, p->Rs, p->norm, w.A, w.src_hi,
+                                     w.src_lo, w.src64, w.phi_out, w.e_out, st);
+        } else {
+            rc = launch_surface_charges(1, p->ndir, p->Nb, p->Bq, p->dirs, w.A, p->Rs, w.img, st);
+            if (!rc && sh.surf_items > 0)
+                rc = launch_surface_pairs(w.sys, 1, sh.surf_items, w.ns, w.src_hi, w.src_lo, w.src64, p->ndir,
+                                          p->dirs, w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st);
+        }
+        if (rc) return rc;
+        if (cnt > 0) {
+            shard_gather_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(t_lo, cnt, w.perm, w.phi_out,
+                                                                                w.e_out, w.idx64, w.pot, w.forces);
+            HSMA_LAUNCHED();
+        }
+    }
+    std::vector<long long> idx(std::max<long long>(cnt, 1));
+    int hst = 0;
+    if (cnt > 0) {
+        HSMA_CUDA_TRY(cudaMemcpyAsync(idx.data(), w.idx64, sizeof(long long) * cnt, cudaMemcpyDeviceToHost, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(phi, w.pot, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(field, w.forces, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
+    }
+    HSMA_CUDA_TRY(cudaMemcpyAsync(&hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+    HSMA_CUDA_TRY(cudaGetLastError());
+    for (long long j = 0; j < cnt; ++j) index[j] = idx[j];
+    *count = cnt;
+    if (!far_stage) {
+        for (int k = 0; k < p->nmon; ++k) phi_mon_out[k] = 0.0;
+        for (long long k = m_lo; k < m_hi; ++k) phi_mon_out[p->mon_perm[k]] = mon[k];
+    }
+    p->last_nsys = 0;  // the workspace no longer holds a whole-system result
+    return map_status(hst);
 }
 
 std::mutex g_scratch_mu;
@@ -1117,6 +1301,19 @@ int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count
     }
     HSMA_CUDA_TRY(cudaMemcpy(host_out, src, nd * sizeof(double), cudaMemcpyDeviceToHost));
     return nd;
+}
+
+// --------------------------------------------------------- target sharding
+int hsma_shard_near(hsma_plan_t pl, const hsma_particles *x, int part, int nparts, int64_t *index, double *phi,
+                    double *field, int64_t *count, double *phi_mon)
+{
+    return run_shard(pl, x, false, part, nparts, nullptr, phi_mon, index, phi, field, count);
+}
+
+int hsma_shard_far(hsma_plan_t pl, const hsma_particles *x, const double *phi_mon, int part, int nparts,
+                   int64_t *index, double *phi, double *field, int64_t *count)
+{
+    return run_shard(pl, x, true, part, nparts, phi_mon, nullptr, index, phi, field, count);
 }
 
 // ------------------------------------------------------------------ tuning

@@ -47,7 +47,11 @@ struct SysDesc {
     long long cnt_off;      // first in-set block count: n_shifts * nblk
     long long hist_off;     // first radix-sort histogram entry: 256 * nblk
     long long tile_off;     // first tile bounding box: ceil(n * n_shifts / tile)
+    long long sp_lo;        // far-field (surface / series) particles: sorted range [sp_lo, sp_lo + sp_n)
+    long long sp_n;
     int gbits;              // Morton grid of 2^gbits cells per axis
+    int pb_lo;              // first particle target block of this call (target sharding)
+    int mb_lo;              // first monitoring target block of this call
     int pad0;
     int nchunks;            // source chunks of the near-field sums
     int ntb;                // target blocks (particles, then monitors)

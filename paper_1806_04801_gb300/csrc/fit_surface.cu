@@ -118,10 +118,11 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
     long long idx[kSurfT];
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
-        long long i = (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
-        idx[t] = (i < sd.n) ? i : -1;
+        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+        const bool ok = i < sd.sp_lo + sd.sp_n;
+        idx[t] = ok ? i : -1;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (i < sd.n) {
+        if (ok) {
             a = src_hi[sd.src_off + i];
             b = src_lo[sd.src_off + i];
         }
@@ -213,10 +214,11 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
     long long idx[kSurfT];
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
-        long long i = (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
-        idx[t] = (i < sd.n) ? i : -1;
+        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+        const bool ok = i < sd.sp_lo + sd.sp_n;
+        idx[t] = ok ? i : -1;
         double4_32a a = make_double4_32a(0, 0, 0, 0);
-        if (i < sd.n) a = src64[sd.src_off + i];
+        if (ok) a = src64[sd.src_off + i];
         r[t][0] = a.x;
         r[t][1] = a.y;
         r[t][2] = a.z;
@@ -402,8 +404,8 @@ __global__ void series_field_kernel(const SysDesc *sys, int nsys, int P, double 
 {
     const int s = blockIdx.y;
     const SysDesc sd = sys[s];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sd.n) return;
+    const long long i = sd.sp_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sd.sp_lo + sd.sp_n) return;
     double x, y, z;
     if (src64) {
         double4_32a p = src64[sd.src_off + i];

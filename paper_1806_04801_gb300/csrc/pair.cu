@@ -163,18 +163,20 @@ __global__ void __launch_bounds__(kThreads, (T == 4 ? 4 : 6)) pair_fp32_kernel(P
         const bool part = it.tb < sd.ntb_part;
         const bool field = part || a.ext_field;
         const long long ntgt = sd.n + a.n_ext;
+        // global block index: particle blocks from pb_lo, external from mb_lo
+        const int gb = part ? sd.pb_lo + it.tb : sd.mb_lo + it.tb - sd.ntb_part;
 
         // targets of this thread
         float th[T][3], tl[T][3];
         long long tidx[T];
         long long tb_lo = 0, tb_hi = 0;  // in-set slots of this block's own particles
         if (part) {
-            tb_lo = (long long)it.tb * TB;
+            tb_lo = (long long)gb * TB;
             tb_hi = tb_lo + TB;
         }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * TB + t * kThreads + tid;
+            long long k = (long long)gb * TB + t * kThreads + tid;
             bool valid = part ? (k < sd.n) : (k < a.n_ext);
             float4 h = make_float4(kFar, kFar, kFar, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
             if (valid) {
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, (T == 4 ? 4 : 6)) pair_fp32_kernel(P
         const bool use_boxes = a.boxes != nullptr && (part || a.ext_boxes != nullptr);
         float4 blo = make_float4(0.f, 0.f, 0.f, 0.f), bhi = blo;
         if (use_boxes) {
-            const float4 *bb = part ? a.boxes + 2 * (sd.tile_off + it.tb) : a.ext_boxes + 2 * (it.tb - sd.ntb_part);
+            const float4 *bb = part ? a.boxes + 2 * (sd.tile_off + gb) : a.ext_boxes + 2 * gb;
             blo = bb[0];
             bhi = bb[1];
         }
@@ -349,17 +351,18 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp64_kernel(PairArgs a)
         const bool part = it.tb < sd.ntb_part;
         const bool field = part || a.ext_field;
         const long long ntgt = sd.n + a.n_ext;
+        const int gb = part ? sd.pb_lo + it.tb : sd.mb_lo + it.tb - sd.ntb_part;
 
         double tx[kT64][3];
         long long tidx[kT64];
         long long tb_lo = 0, tb_hi = 0;
         if (part) {
-            tb_lo = (long long)it.tb * kTB64;
+            tb_lo = (long long)gb * kTB64;
             tb_hi = tb_lo + kTB64;
         }
 #pragma unroll
         for (int t = 0; t < kT64; ++t) {
-            long long k = (long long)(part ? it.tb : it.tb - sd.ntb_part) * kTB64 + t * kThreads + tid;
+            long long k = (long long)gb * kTB64 + t * kThreads + tid;
             bool valid = part ? (k < sd.n) : (k < a.n_ext);
             double4_32a p = make_double4_32a(1e4, 1e4, 1e4, 0.0);
             if (valid) p = part ? a.src64[sd.src_off + k] : a.ext64[k];

@@ -83,6 +83,10 @@ SIGNATURES = {
     "hsma_autotune": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_particles), ctypes.c_char_p,
                            ctypes.POINTER(hsma_tuning)]),
     "hsma_plan_load_tuning": (_I, [_VP, ctypes.c_char_p]),
+    "hsma_shard_near": (_I, [_VP, ctypes.POINTER(hsma_particles), _I, _I, _VP, _VP, _VP,
+                             ctypes.POINTER(_I64), _VP]),
+    "hsma_shard_far": (_I, [_VP, ctypes.POINTER(hsma_particles), _VP, _I, _I, _VP, _VP, _VP,
+                            ctypes.POINTER(_I64)]),
 }
 
 _LIB = None
@@ -275,6 +279,42 @@ class Plan:
                                                _ptr_and_dev(p)[0] if p is not None else None, st.ctypes.data)
         _check(rc, "hsma_energy_forces_batched")
         return e, f, p, st
+
+    # ---------------------------------------------------- target sharding
+    def _shard_args(self, xyz, q):
+        pxyz, dev = _ptr_and_dev(xyz)
+        pq, _ = _ptr_and_dev(q)
+        n = int(q.shape[0])
+        return hsma_particles(n, pxyz, pq, 1 if dev else 0), n
+
+    def shard_near(self, xyz, q, part: int, nparts: int):
+        """hsma_shard_near: (index, phi_in, E_in, phi_mon) for this part
+        (host arrays; phi_mon is zero outside the part's monitoring slice)."""
+        part_s, n = self._shard_args(xyz, q)
+        idx = np.empty(n, dtype=np.int64)
+        phi = np.empty(n)
+        fld = np.empty((n, 3))
+        mon = np.empty(self.info()["n_mon_targets"])
+        cnt = ctypes.c_int64()
+        _check(_lib().hsma_shard_near(self._h, ctypes.byref(part_s), int(part), int(nparts), idx.ctypes.data,
+                                      phi.ctypes.data, fld.ctypes.data, ctypes.byref(cnt), mon.ctypes.data),
+               "hsma_shard_near")
+        k = cnt.value
+        return idx[:k].copy(), phi[:k].copy(), fld[:k].copy(), mon
+
+    def shard_far(self, xyz, q, phi_mon, part: int, nparts: int):
+        """hsma_shard_far: (index, phi_out, E_out) for this part."""
+        part_s, n = self._shard_args(xyz, q)
+        mon = np.ascontiguousarray(phi_mon, dtype=np.float64)
+        idx = np.empty(n, dtype=np.int64)
+        phi = np.empty(n)
+        fld = np.empty((n, 3))
+        cnt = ctypes.c_int64()
+        _check(_lib().hsma_shard_far(self._h, ctypes.byref(part_s), mon.ctypes.data, int(part), int(nparts),
+                                     idx.ctypes.data, phi.ctypes.data, fld.ctypes.data, ctypes.byref(cnt)),
+               "hsma_shard_far")
+        k = cnt.value
+        return idx[:k].copy(), phi[:k].copy(), fld[:k].copy()
 
     # ------------------------------------------------------------ tuning
     def set_tuning(self, pair_variant=None, items_per_slot=None):

@@ -337,3 +337,30 @@ def test_series_far_field(bc):
         Ui, Fi, _, _ = plan.energy_forces(dx, dq)
     # mapping accuracy of the surface images (quadrature + O(dr^2))
     assert abs(Ui - U) <= 1e-7 * abs(U)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("bc", ["periodic", "grounded"])
+def test_target_sharded_stages(prec, bc):
+    """hsma_shard_near / hsma_shard_far for every part of a split step (all
+    parts on this one GPU, exchanges as plain sums) reproduce
+    hsma_energy_forces."""
+    from paper_1806_04801_gb300 import sharded
+    if bc == "periodic":
+        w = I.SMALL_PERIODIC
+        xyz, q = I.uniform_pm1(5000, w.box, seed_offset=402)
+    else:
+        w = I.Workload("grounded-small", (1.0, 1.0, 2.0), I.GROUNDED, 10, I.GROUNDED_CAVITY.R, 6000, 1500)
+        xyz, q = I.uniform_pm1(3000, w.box, seed_offset=403, margin=0.05)
+    dx, dq = to_dev(xyz, q)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+        U0, F0, P0, _ = plan.energy_forces(dx, dq, potentials=True)
+        F0 = F0.cpu().numpy()
+        for nparts in (1, 2, 3, 8):
+            U, F, pot = sharded.shard_update_local(sharded.GpuBackend(plan), dx, dq, nparts)
+            tol = 1e-12 if prec == "fp64" else 1e-7
+            assert abs(U - U0) <= tol * abs(U0), (nparts, U, U0)
+            assert rms(F - F0) <= tol * 10 * rms(F0), nparts
+        # host inputs give the same split
+        U_h, F_h, _ = sharded.shard_update_local(sharded.GpuBackend(plan), xyz, q, 2)
+        assert abs(U_h - U0) <= (1e-12 if prec == "fp64" else 1e-7) * abs(U0)

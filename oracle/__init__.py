@@ -72,6 +72,9 @@ def _declare(L):
     L.hsmo_ewald.restype = None
     L.hsmo_ewald.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
                              ctypes.c_int, _dp, _dp]
+    L.hsmo_ewald_sf.restype = None
+    L.hsmo_ewald_sf.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_int, _dp, _dp]
 
 
 def _d(a):
@@ -181,4 +184,17 @@ def ewald(xyz, q, L, beta: float, nreal: int, kmax: int):
     fld = np.empty((n, 3))
     lib().hsmo_ewald(n, _ptr(xyz), _ptr(q), _ptr(L), float(beta), int(nreal), int(kmax),
                      _ptr(pot), _ptr(fld))
+    return pot, fld
+
+
+def ewald_sf(xyz, q, L, beta: float, nreal: int, kmax: int):
+    """Ewald as ``ewald`` with structure factors (O(N K) reciprocal part)."""
+    xyz = _d(xyz).reshape(-1, 3)
+    q = _d(q)
+    L = _d(L)
+    n = xyz.shape[0]
+    pot = np.empty(n)
+    fld = np.empty((n, 3))
+    lib().hsmo_ewald_sf(n, _ptr(xyz), _ptr(q), _ptr(L), float(beta), int(nreal), int(kmax),
+                        _ptr(pot), _ptr(fld))
     return pot, fld

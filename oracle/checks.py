@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import ewald
+from . import ewald, ewald_sf
 
 
 def _ewald_params(L):
@@ -75,3 +75,12 @@ def nacl_lattice(n_side: int, L: float):
 def madelung_from_energy(U, n_ions: int, a: float, qabs: float = 1.0):
     """U = -(N/2) M q^2 / a for a rock-salt lattice, so M = -2 a U / (N q^2)."""
     return -2.0 * a * U / (n_ions * qabs * qabs)
+
+
+def ewald_periodic_fast(xyz, q, L):
+    """ewald_periodic with the structure-factor reciprocal sum (for a few
+    thousand charges)."""
+    beta, nreal, kmax = _ewald_params(L)
+    pot, fld = ewald_sf(xyz, q, L, beta, nreal, kmax)
+    q = np.asarray(q, dtype=np.float64)
+    return pot, fld, 0.5 * float(np.dot(q, pot))

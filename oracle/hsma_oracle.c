@@ -442,3 +442,64 @@ void hsmo_ewald(long n, const double *xyz, const double *q, const double L[3], d
             for (int a = 0; a < 3; ++a) field[3 * i + a] = e[a];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The same Ewald sum as hsmo_ewald, with the reciprocal part through        */
+/* structure factors S(k) = sum_j q_j exp(i k.r_j) (O(N K) instead of        */
+/* O(N^2 K)) and the real part over |n_a| <= nreal cells; for larger checks. */
+/* ------------------------------------------------------------------------ */
+void hsmo_ewald_sf(long n, const double *xyz, const double *q, const double L[3], double beta, int nreal,
+                   int kmax, double *pot, double *field)
+{
+    double V = L[0] * L[1] * L[2];
+    for (long i = 0; i < n; ++i) {
+        double phi = 0.0, e[3] = {0.0, 0.0, 0.0};
+        for (long j = 0; j < n; ++j)
+            for (int nx = -nreal; nx <= nreal; ++nx)
+                for (int ny = -nreal; ny <= nreal; ++ny)
+                    for (int nz = -nreal; nz <= nreal; ++nz) {
+                        if (i == j && nx == 0 && ny == 0 && nz == 0) continue;
+                        double d[3] = {xyz[3 * i] - xyz[3 * j] - nx * L[0],
+                                       xyz[3 * i + 1] - xyz[3 * j + 1] - ny * L[1],
+                                       xyz[3 * i + 2] - xyz[3 * j + 2] - nz * L[2]};
+                        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                        if (beta * r > 7.0) continue; /* erfc(7) ~ 4e-23 */
+                        double ec = erfc(beta * r);
+                        phi += q[j] * ec / r;
+                        double g = q[j] * (ec + 2.0 * beta * r / sqrt(M_PI) * exp(-beta * beta * r * r)) /
+                                   (r * r * r);
+                        for (int a = 0; a < 3; ++a) e[a] += g * d[a];
+                    }
+        pot[i] = phi - 2.0 * beta * q[i] / sqrt(M_PI);
+        if (field)
+            for (int a = 0; a < 3; ++a) field[3 * i + a] = e[a];
+    }
+    double *c = (double *)malloc(sizeof(double) * n), *s = (double *)malloc(sizeof(double) * n);
+    for (int mx = -kmax; mx <= kmax; ++mx)
+        for (int my = -kmax; my <= kmax; ++my)
+            for (int mz = -kmax; mz <= kmax; ++mz) {
+                if (mx == 0 && my == 0 && mz == 0) continue;
+                double k[3] = {2.0 * M_PI * mx / L[0], 2.0 * M_PI * my / L[1], 2.0 * M_PI * mz / L[2]};
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                double f = 4.0 * M_PI / V * exp(-k2 / (4.0 * beta * beta)) / k2;
+                if (f < 1e-300) continue;
+                double Sc = 0.0, Ss = 0.0;
+                for (long j = 0; j < n; ++j) {
+                    double arg = k[0] * xyz[3 * j] + k[1] * xyz[3 * j + 1] + k[2] * xyz[3 * j + 2];
+                    c[j] = cos(arg);
+                    s[j] = sin(arg);
+                    Sc += q[j] * c[j];
+                    Ss += q[j] * s[j];
+                }
+                for (long i = 0; i < n; ++i) {
+                    /* sum_j q_j cos(k.(r_i - r_j)) = c_i Sc + s_i Ss; the sin form for the field */
+                    pot[i] += f * (c[i] * Sc + s[i] * Ss);
+                    if (field) {
+                        double sn = s[i] * Sc - c[i] * Ss;
+                        for (int a = 0; a < 3; ++a) field[3 * i + a] += f * k[a] * sn;
+                    }
+                }
+            }
+    free(c);
+    free(s);
+}

@@ -189,3 +189,15 @@ def test_series_far_field_matches_surface_images():
     # both against Ewald
     _, fld, U = checks.ewald_periodic(xyz, q, L)
     assert abs(ser["energy"] - U) <= 1e-7 * abs(U)
+
+
+def test_structure_factor_ewald_equals_pairwise_ewald():
+    L = np.array([1.0, 1.0, 1.3])
+    xyz, q = inputs.random_neutral(20, L, 44)
+    p1, f1, U1 = checks.ewald_periodic(xyz, q, L)
+    p2, f2, U2 = checks.ewald_periodic_fast(xyz, q, L)
+    np.testing.assert_allclose(p2, p1, rtol=0, atol=1e-12 * np.abs(p1).max())
+    np.testing.assert_allclose(f2, f1, rtol=0, atol=1e-11 * np.abs(f1).max())
+    xyz, q, a = checks.nacl_lattice(MADELUNG["n_side"], MADELUNG["L"])
+    _, _, U = checks.ewald_periodic_fast(xyz, q, np.full(3, MADELUNG["L"]))
+    assert abs(checks.madelung_from_energy(U, len(q), a) - MADELUNG["madelung_constant"]) < 1e-12

@@ -219,9 +219,11 @@ int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *ph
 /* Work decomposition of the near-field pair kernel (no counterpart in the
  * paper; it changes speed, not results beyond rounding of the chunk
  * grouping):
- *   pair_variant    targets per thread of the FP32 kernel: 4 (blocks and
- *                   source tiles of 512) or 2 (256: more CTAs per SM, finer
- *                   work items); ignored in FP64
+ *   pair_variant    FP32 kernel blocking: 4 = four targets per thread
+ *                   (blocks and source tiles of 512) at 4 CTAs per SM;
+ *                   5 = the same at 5 CTAs per SM (fewer registers);
+ *                   2 = two targets per thread (blocks and tiles of 256) at
+ *                   6 CTAs per SM; ignored in FP64
  *   items_per_slot  work items per resident CTA slot (source chunks are sized
  *                   so that a call has about this many items per slot)
  *   ms              time measured by hsma_autotune (0 otherwise)
@@ -242,7 +244,7 @@ int hsma_plan_set_tuning(hsma_plan_t plan, const hsma_tuning *t);
 int hsma_plan_get_tuning(hsma_plan_t plan, int nsys, const int64_t *offsets, hsma_tuning *out);
 
 /* Autotuner: runs the update step on this batch for each candidate
- * (pair_variant 4 and 2, items_per_slot 8, 16, 24, 48), keeps the fastest as
+ * (pair_variant 4, 5 and 2, items_per_slot 8, 16, 24, 48), keeps the fastest as
  * the plan's entry for this work size, returns it in *best, and appends it as
  * one JSON line to cache_path (if not NULL).  Device inputs are recommended
  * (host inputs add their copies to every timing). */

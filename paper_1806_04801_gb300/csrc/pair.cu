@@ -121,8 +121,10 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
     }
 }
 
-template <int T>
-__global__ void __launch_bounds__(kThreads, (T == 4 ? 4 : 6)) pair_fp32_kernel(PairArgs a)
+// MINB: CTAs per SM the register allocation must allow (4 or 5 for T = 4,
+// 6 for T = 2); the autotuner picks among these variants.
+template <int T, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
 {
     constexpr int TB = kThreads * T;  // targets per block
     constexpr int TILE = TB;          // sources per tile
@@ -478,6 +480,9 @@ int pair_targets_per_block(int precision, int variant)
     return precision == HSMA_FP64 ? kTB64 : kThreads * (variant == 2 ? 2 : 4);
 }
 
+// variant: 4 = four targets per thread at >= 4 CTAs/SM; 5 = four targets at
+// >= 5 CTAs/SM (fewer registers); 2 = two targets at >= 6 CTAs/SM.
+
 static size_t pair_smem(int precision, int variant)
 {
     return precision == HSMA_FP64 ? 2 * kTile64 * sizeof(double4_32a)
@@ -497,7 +502,9 @@ int pair_max_ctas_per_sm(int precision, int variant)
 {
     const size_t sm = pair_smem(precision, variant);
     if (precision == HSMA_FP64) return occupancy_of(pair_fp64_kernel, sm);
-    return variant == 2 ? occupancy_of(pair_fp32_kernel<2>, sm) : occupancy_of(pair_fp32_kernel<4>, sm);
+    if (variant == 2) return occupancy_of(pair_fp32_kernel<2, 6>, sm);
+    if (variant == 5) return occupancy_of(pair_fp32_kernel<4, 5>, sm);
+    return occupancy_of(pair_fp32_kernel<4, 4>, sm);
 }
 
 // The dynamic shared-memory attribute is set by pair_max_ctas_per_sm, which
@@ -510,9 +517,11 @@ int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStr
     if (precision == HSMA_FP64)
         pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
     else if (variant == 2)
-        pair_fp32_kernel<2><<<grid, kThreads, sm, st>>>(a);
+        pair_fp32_kernel<2, 6><<<grid, kThreads, sm, st>>>(a);
+    else if (variant == 5)
+        pair_fp32_kernel<4, 5><<<grid, kThreads, sm, st>>>(a);
     else
-        pair_fp32_kernel<4><<<grid, kThreads, sm, st>>>(a);
+        pair_fp32_kernel<4, 4><<<grid, kThreads, sm, st>>>(a);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

@@ -58,6 +58,7 @@ extern "C" {
 #define HSMA_E_NOT_FOUND (-9)    /* unknown ticket / item                            */
 #define HSMA_E_AGAIN (-10)       /* serving: result not ready yet                    */
 #define HSMA_E_CAPACITY (-11)    /* serving: request larger than the memory budget   */
+#define HSMA_E_CANCELLED (-12)   /* serving: request cancelled before it ran          */
 
 /* ------------------------------------------------------------ parameters */
 typedef struct hsma_plan_s *hsma_plan_t;
@@ -286,7 +287,7 @@ typedef struct {
 } hsma_request_info;
 
 typedef struct {
-    int64_t completed, failed, queued, batches;
+    int64_t completed, failed, cancelled, queued, batches;
     double mean_batch;        /* systems per batched pass                                */
     double elapsed_s;         /* first submit -> last completion                         */
     size_t hbm_held_bytes, hbm_budget_bytes;
@@ -308,6 +309,11 @@ int hsma_server_submit(hsma_server_t srv, int64_t n, const double *xyz, const do
  * (HSMA_E_NOT_FOUND afterwards). */
 int hsma_server_result(hsma_server_t srv, int64_t ticket, int wait, double *energy, double *forces,
                        hsma_request_info *info);
+
+/* Withdraw a queued request: HSMA_OK (its result then reports
+ * HSMA_E_CANCELLED), HSMA_E_AGAIN if it already runs or ran, HSMA_E_NOT_FOUND
+ * for an unknown or collected ticket. */
+int hsma_server_cancel(hsma_server_t srv, int64_t ticket);
 
 int hsma_server_stats(hsma_server_t srv, hsma_server_stats_t *stats);
 

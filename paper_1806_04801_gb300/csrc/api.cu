@@ -941,6 +941,7 @@ const char *hsma_strerror(int code)
         case HSMA_E_NOT_FOUND: return "not found";
         case HSMA_E_AGAIN: return "not ready";
         case HSMA_E_CAPACITY: return "request exceeds the memory budget";
+        case HSMA_E_CANCELLED: return "request cancelled";
         default: return "unknown error";
     }
 }

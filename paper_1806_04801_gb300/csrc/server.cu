@@ -55,7 +55,7 @@ struct hsma_server_s {
     std::unordered_map<int64_t, Request *> all;
     int64_t next_id = 1;
     bool stop = false;
-    long long completed = 0, failed = 0, batches = 0, batched_systems = 0;
+    long long completed = 0, failed = 0, batches = 0, batched_systems = 0, cancelled = 0;
     Clock::time_point t0;
     bool t0_set = false;
     Clock::time_point t_last_done;
@@ -274,12 +274,33 @@ int hsma_server_result(hsma_server_t s, int64_t ticket, int wait, double *energy
     return code;
 }
 
+int hsma_server_cancel(hsma_server_t s, int64_t ticket)
+{
+    if (!s) return HSMA_E_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return HSMA_E_NOT_FOUND;
+    Request *r = it->second;
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+        if (*q == r) {
+            s->queue.erase(q);
+            r->status = HSMA_E_CANCELLED;
+            r->t_done = Clock::now();
+            r->t_start = r->t_done;
+            s->cancelled++;
+            s->cv_done.notify_all();
+            return HSMA_OK;
+        }
+    return HSMA_E_AGAIN;  // already running or finished
+}
+
 int hsma_server_stats(hsma_server_t s, hsma_server_stats_t *st)
 {
     if (!s || !st) return HSMA_E_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     st->completed = s->completed;
     st->failed = s->failed;
+    st->cancelled = s->cancelled;
     st->queued = (int64_t)s->queue.size();
     st->batches = s->batches;
     st->mean_batch = s->batches ? (double)s->batched_systems / s->batches : 0.0;

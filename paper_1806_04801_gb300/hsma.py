@@ -431,7 +431,8 @@ class hsma_request_info(ctypes.Structure):
 
 
 class hsma_server_stats_t(ctypes.Structure):
-    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("queued", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("elapsed_s", ctypes.c_double),
                 ("hbm_held_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t)]
 
@@ -443,6 +444,7 @@ SIGNATURES.update({
     "hsma_server_submit": (_I, [_VP, _I64, _VP, _VP, ctypes.POINTER(_I64)]),
     "hsma_server_result": (_I, [_VP, _I64, _I, ctypes.POINTER(_D), _VP, ctypes.POINTER(hsma_request_info)]),
     "hsma_server_stats": (_I, [_VP, ctypes.POINTER(hsma_server_stats_t)]),
+    "hsma_server_cancel": (_I, [_VP, _I64]),
     "hsma_server_destroy": (None, [_VP]),
 })
 
@@ -482,6 +484,10 @@ class Server:
         code = _lib().hsma_server_result(self._h, int(ticket), 1 if wait else 0, ctypes.byref(e),
                                          f.ctypes.data if f is not None else None, ctypes.byref(info))
         return code, e.value, f, {k: getattr(info, k) for k, _ in hsma_request_info._fields_}
+
+    def cancel(self, ticket: int) -> int:
+        """hsma_server_cancel: 0 if withdrawn, -10 if already running/ran."""
+        return int(_lib().hsma_server_cancel(self._h, int(ticket)))
 
     def stats(self) -> dict:
         st = hsma_server_stats_t()

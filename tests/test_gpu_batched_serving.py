@@ -193,3 +193,24 @@ def test_autotuner_and_both_kernel_variants(tmp_path):
         E, F, _, _ = plan2.energy_forces_batched(dx, dq, off)
         for i in range(len(systems)):
             assert rel_energy_err(E[i], E0[i], systems[i][1]) <= 1e-6
+
+
+def test_serving_cancellation():
+    """Requests withdrawn while queued report the cancellation code and never
+    run; the rest of the stream is served normally."""
+    w = I.SERVING_PERIODIC
+    reqs = [I.uniform_pm1(int(n), w.box, seed_offset=120 + i) for i, n in enumerate([60000] * 2 + [2000] * 10)]
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, lanes=1, max_batch=1) as srv:
+        tickets = [srv.submit(*r) for r in reqs]
+        # the tail is still queued behind the two large requests: withdraw every other one
+        withdrawn = [t for i, t in enumerate(tickets) if i >= 4 and i % 2 == 0]
+        codes = {t: srv.cancel(t) for t in withdrawn}
+        for t, (x, q) in zip(tickets, reqs):
+            code, E, F, info = srv.result(t, n=len(q))
+            if t in withdrawn and codes[t] == 0:
+                assert code == -12
+            else:
+                assert code == 0 and np.isfinite(E)
+        st = srv.stats()
+        assert st["cancelled"] == sum(1 for c in codes.values() if c == 0) >= 1
+        assert st["completed"] + st["cancelled"] == len(reqs)

@@ -38,8 +38,9 @@ RECIPE_SMS = 152
 RECIPE_MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) of one full-size pair_fp32_kernel launch of the
 # periodic N=100000 workload, from the ncu capture summarised in
-# profiles/pair_fp32_kernel_periodic_N100000_dram.md (current kernel build).
-PAIR_FP32_TRAFFIC_BYTES = {100_000: 237.46e6}
+# profiles/pair_fp32_kernel_periodic_N100000_dram.md (current kernel build),
+# keyed by (N, pair variant, items per slot) of the captured launch.
+PAIR_FP32_TRAFFIC_BYTES = {(100_000, 2, 48): 357.72e6}
 OPS_SURFACE = 45                 # FP32 lane instructions per particle-direction pair of the surface kernel
 
 
@@ -56,6 +57,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
     ap.add_argument("--workload", default="periodic", choices=["periodic", "batched", "serving", "grounded"])
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the Poisson trace")
+    ap.add_argument("--tuning", default=None,
+                    help="V,I: fix the pair kernel variant and items per slot instead of autotuning "
+                         "(profiling runs use this so the captured launch is the timed configuration)")
     return ap.parse_args()
 
 
@@ -400,7 +404,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    tuning = plan.autotune(dx, dq)
+    if args.tuning:
+        v, i = (int(t) for t in args.tuning.split(","))
+        plan.set_tuning(v, i)
+        tuning = {"pair_variant": v, "items_per_slot": i, "ms": None, "fixed": True}
+    else:
+        tuning = plan.autotune(dx, dq)
     for _ in range(args.warmup):
         plan.energy_forces(dx, dq)
     torch.cuda.synchronize()
@@ -516,7 +525,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "pair_fp32_kernel" if args.precision != "fp64" else "pair_fp64_kernel",
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T FP32 lane-instructions/s", "frac": achieved / peak_ops,
-                     "traffic": (PAIR_FP32_TRAFFIC_BYTES.get(n) if args.precision == "fp32" else None),
+                     "traffic": (PAIR_FP32_TRAFFIC_BYTES.get((n, tuning["pair_variant"], tuning["items_per_slot"]))
+                                 if args.precision == "fp32" else None),
                      "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
                                    f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",

@@ -66,7 +66,7 @@ __device__ __forceinline__ Item decode_item(const PairArgs &a, int item)
 // only: their rounding (<= 2^-24 |x|) then changes each distance by a relative
 // ~1e-6 or less, while the closest pairs -- where an absolute error of
 // ~1e-7 would matter -- always take the split form.
-template <int T, bool FIELD, int SKIP, bool SPLIT>
+template <int T, int UNROLL, bool FIELD, int SKIP, bool SPLIT>
 __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const float4 *__restrict__ sl, int cnt_pad,
                                        const float (&th)[T][3], const float (&tl)[T][3],
                                        const int (&self_rel)[T], float2 (&phi)[T], float2 (&g)[T][3])
@@ -78,7 +78,7 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
         float pa[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) pa[t] = 0.f;
-#pragma unroll 4
+#pragma unroll UNROLL
         for (int s = 0; s < kFold; ++s) {
             const float4 h = sh[s0 + s];
             const float4 l = SPLIT ? sl[s0 + s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -126,6 +126,9 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
 template <int T, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
 {
+    // source-loop unrolling per variant (measured: 4 targets at 4 CTAs/SM
+    // prefers 4, at 5 CTAs/SM 8, two targets a full unroll)
+    constexpr int UNROLL = (T == 2) ? kFold : (MINB >= 5 ? 8 : 4);
     constexpr int TB = kThreads * T;  // targets per block
     constexpr int TILE = TB;          // sources per tile
     extern __shared__ __align__(128) float4 smem32[];
@@ -261,20 +264,20 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
             }
             if (field) {
                 if (far)
-                    tile32<T, true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 1)
-                    tile32<T, true, 1, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, true, 1, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 2)
-                    tile32<T, true, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, true, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<T, true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, true, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             } else {
                 if (far)
-                    tile32<T, false, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, false, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else if (skip == 2)
-                    tile32<T, false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, false, 2, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
                 else
-                    tile32<T, false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
+                    tile32<T, UNROLL, false, 0, true>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
             }
             __syncthreads();
             if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);

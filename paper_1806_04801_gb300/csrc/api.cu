@@ -97,7 +97,8 @@ struct hsma_plan_s {
     int far_field = 0;            // 0: surface images (Sec. II.B); 1: direct series at the particles
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
-    int num_sms, ctas[3], ctas_v2, ctas_v5;
+    int num_sms, ctas[3];
+    int ctas_var[16] = {};  // FP32 pair kernel: resident CTAs per SM, by variant code
     // tuning of the pair kernel: a fixed choice, or entries per work bucket
     bool tune_fixed = false;
     hsma_tuning tune_value{4, 24, 0.0};
@@ -208,7 +209,7 @@ int ensure_pinned(hsma_plan_s *p, size_t bytes)
 int tuned_ctas(const hsma_plan_s *p, int precision, int variant)
 {
     if (precision == HSMA_FP64) return p->ctas[0];
-    return variant == 2 ? p->ctas_v2 : (variant == 5 ? p->ctas_v5 : p->ctas[1]);
+    return (variant > 0 && variant < 16 && p->ctas_var[variant] > 0) ? p->ctas_var[variant] : p->ctas[1];
 }
 
 // Pair work of a batch (targets x estimated in-set sources), and its bucket
@@ -246,7 +247,7 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
 {
     sh->nsys = nsys;
     sh->sys.assign(nsys, SysDesc{});
-    sh->variant = (tu.pair_variant == 2 || tu.pair_variant == 5) ? tu.pair_variant : 4;
+    sh->variant = pair_variant_valid(tu.pair_variant) ? tu.pair_variant : 4;
     const int TB = pair_targets_per_block(precision, sh->variant);
     const int STB = surface_targets_per_block();
     const int tile = TB;
@@ -480,7 +481,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.ext_field = 0;
     pa.ext_skip_zero = 0;
     pa.boxes = w.boxes;
-    pa.ext_boxes = w.boxes ? (sh.variant == 2 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
+    pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
     pa.stall_test = p->stall_test;
     pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
@@ -824,7 +825,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
         pa.ext_field = 0;
         pa.ext_skip_zero = 0;
         pa.boxes = w.boxes;
-        pa.ext_boxes = w.boxes ? (sh.variant == 2 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
+        pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
         pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
         pa.partials = w.partials;
         pa.next_item = w.ctrl;
@@ -1019,8 +1020,8 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     pl->num_sms = prop.multiProcessorCount;
     pl->ctas[0] = pair_max_ctas_per_sm(HSMA_FP64);
     pl->ctas[1] = pl->ctas[2] = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 4);
-    pl->ctas_v2 = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 2);
-    pl->ctas_v5 = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 5);
+    for (int v = 1; v < 16; ++v)
+        if (pair_variant_valid(v)) pl->ctas_var[v] = pair_max_ctas_per_sm(HSMA_FP32_ACC64, v);
     snprintf(pl->device_name, sizeof(pl->device_name), "%s", prop.name);
 
     // image shift table: k = 0 first, then lexicographic (kx, ky, kz)
@@ -1326,7 +1327,7 @@ int hsma_plan_set_tuning(hsma_plan_t pl, const hsma_tuning *t)
         pl->tune_fixed = false;
         return HSMA_OK;
     }
-    if ((t->pair_variant != 2 && t->pair_variant != 4 && t->pair_variant != 5) || t->items_per_slot < 1 ||
+    if (!pair_variant_valid(t->pair_variant) || t->items_per_slot < 1 ||
         t->items_per_slot > 4096)
         return HSMA_E_ARG;
     pl->tune_fixed = true;
@@ -1353,9 +1354,9 @@ int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_p
     const hsma_tuning value0 = pl->tune_value;
     std::vector<double> energies(nsys);
     std::vector<hsma_tuning> cands;
-    const int variants[3] = {4, 5, 2};
+    const int variants[6] = {4, 5, 2, 12, 13, 14};
     const int items[4] = {8, 16, 24, 48};
-    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 3); ++v)
+    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 6); ++v)
         for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
     hsma_tuning win{4, 24, 1e300};
     int rc = HSMA_OK;
@@ -1414,7 +1415,7 @@ int hsma_plan_load_tuning(hsma_plan_t pl, const char *cache_path)
                          dev, &bc, &P, &K, &F2, &prec, &bucket, &var, &ips, &ms);
         if (got != 10) continue;
         if (strcmp(dev, pl->device_name) || bc != pl->bc || P != pl->P || K != pl->K || F2 != pl->F2 ||
-            prec != pl->precision || (var != 2 && var != 4 && var != 5) || ips < 1)
+            prec != pl->precision || !pair_variant_valid(var) || ips < 1)
             continue;
         bool replaced = false;
         for (auto &e : pl->tune_entries)

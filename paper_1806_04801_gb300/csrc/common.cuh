@@ -260,6 +260,7 @@ struct PairArgs {
 // variant (FP32 form): targets per thread, 4 (blocks and tiles of 512) or 2
 // (blocks and tiles of 256).
 int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStream_t st);
+bool pair_variant_valid(int variant);
 int pair_targets_per_block(int precision, int variant = 4);
 int pair_max_ctas_per_sm(int precision, int variant = 4);
 int launch_partial_reduce(const SysDesc *sys, int nsys, long long max_tgt, int n_ext, const float4 *partials,

@@ -33,6 +33,7 @@ constexpr int kT64 = 2;
 constexpr int kTB64 = kThreads * kT64;
 constexpr int kTile64 = 256;
 constexpr int kFold = 32;               // potential fold interval (sources)
+constexpr int kFold2 = 64;              // packed loop: 32 sources per lane
 constexpr float kFar = 1.0e4f;          // position of zero-charge padding sources
 
 struct Item {
@@ -121,19 +122,114 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
     }
 }
 
+// Packed form of tile32 for two sources at a time (f32x2 instructions: one
+// issue slot for two lanes of FP32 work).  The tile is pair-interleaved:
+// ph[2p] = (x_2p, x_2p+1, y_2p, y_2p+1), ph[2p+1] = (z_2p, z_2p+1, q_2p, q_2p+1),
+// the same for the low words in pl; nth / ntl hold the negated target words
+// twice.  Each lane does the operations of tile32 in the same order, except
+// that the potential takes q/r with one fused multiply-add.  A lane sums 32
+// sources of a 64-source fold interval (even and odd slots), the same FP32
+// run length as tile32; the two lane sums are added and folded with one
+// TwoSum.
+template <int T, int UNROLL, bool FIELD, int SKIP, bool SPLIT>
+__device__ __forceinline__ void tile32x2(const float4 *__restrict__ ph, const float4 *__restrict__ pl, int cnt_pad,
+                                         const float2 (&nth)[T][3], const float2 (&ntl)[T][3],
+                                         const int (&self_rel)[T], float2 (&phi)[T], float2 (&g)[T][3])
+{
+    float2 ga[T][3];
+#pragma unroll
+    for (int t = 0; t < T; ++t) ga[t][0] = ga[t][1] = ga[t][2] = make_float2(0.f, 0.f);
+    for (int s0 = 0; s0 < cnt_pad; s0 += kFold2) {
+        float2 pa[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) pa[t] = make_float2(0.f, 0.f);
+#pragma unroll UNROLL
+        for (int s = 0; s < kFold2; s += 2) {
+            const float4 a = ph[s0 + s], b = ph[s0 + s + 1];
+            const float2 sx = make_float2(a.x, a.y), sy = make_float2(a.z, a.w);
+            const float2 sz = make_float2(b.x, b.y), sq = make_float2(b.z, b.w);
+            float2 lx = make_float2(0.f, 0.f), ly = lx, lz = lx;
+            if (SPLIT) {
+                const float4 c = pl[s0 + s], d = pl[s0 + s + 1];
+                lx = make_float2(c.x, c.y);
+                ly = make_float2(c.z, c.w);
+                lz = make_float2(d.x, d.y);
+            }
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                float2 dx, dy, dz;
+                if (SPLIT) {
+                    dx = __fadd2_rn(__fadd2_rn(sx, nth[t][0]), __fadd2_rn(lx, ntl[t][0]));
+                    dy = __fadd2_rn(__fadd2_rn(sy, nth[t][1]), __fadd2_rn(ly, ntl[t][1]));
+                    dz = __fadd2_rn(__fadd2_rn(sz, nth[t][2]), __fadd2_rn(lz, ntl[t][2]));
+                } else {
+                    dx = __fadd2_rn(sx, nth[t][0]);
+                    dy = __fadd2_rn(sy, nth[t][1]);
+                    dz = __fadd2_rn(sz, nth[t][2]);
+                }
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                float2 ri = make_float2(rsqrt_sfu(r2.x), rsqrt_sfu(r2.y));
+                if (SKIP == 1) {
+                    ri.x = (s0 + s == self_rel[t]) ? 0.f : ri.x;
+                    ri.y = (s0 + s + 1 == self_rel[t]) ? 0.f : ri.y;
+                }
+                if (SKIP == 2) {
+                    ri.x = (r2.x > 0.f) ? ri.x : 0.f;
+                    ri.y = (r2.y > 0.f) ? ri.y : 0.f;
+                }
+                pa[t] = __ffma2_rn(sq, ri, pa[t]);
+                if (FIELD) {
+                    const float2 qr3 = __fmul2_rn(__fmul2_rn(__fmul2_rn(sq, ri), ri), ri);
+                    ga[t][0] = __ffma2_rn(qr3, dx, ga[t][0]);
+                    ga[t][1] = __ffma2_rn(qr3, dy, ga[t][1]);
+                    ga[t][2] = __ffma2_rn(qr3, dz, ga[t][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) phi[t] = df_add(phi[t], pa[t].x + pa[t].y);
+    }
+    if (FIELD) {
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g[t][c] = df_add(g[t][c], ga[t][c].x + ga[t][c].y);
+    }
+}
+
+// Pair-interleave a staged tile (one float4 per source) into the layout of
+// tile32x2; slots cnt..cnt_pad-1 become the padding source `pad`.
+__device__ __forceinline__ void interleave_pairs(const float4 *__restrict__ src, float4 *__restrict__ dst, int cnt,
+                                                 int cnt_pad, float4 pad, int tid)
+{
+    for (int p = tid; 2 * p < cnt_pad; p += kThreads) {
+        const int i = 2 * p;
+        const float4 a = i < cnt ? src[i] : pad;
+        const float4 b = i + 1 < cnt ? src[i + 1] : pad;
+        dst[i] = make_float4(a.x, b.x, a.y, b.y);
+        dst[i + 1] = make_float4(a.z, b.z, a.w, b.w);
+    }
+}
+
 // MINB: CTAs per SM the register allocation must allow (4 or 5 for T = 4,
-// 6 for T = 2); the autotuner picks among these variants.
-template <int T, int MINB>
+// 5 or 6 for T = 2); X2: packed two-source loop (tile32x2) on a
+// pair-interleaved copy of each staged tile.  The autotuner picks among these
+// variants.
+template <int T, int MINB, bool X2>
 __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
 {
     // source-loop unrolling per variant (measured: 4 targets at 4 CTAs/SM
     // prefers 4, at 5 CTAs/SM 8, two targets a full unroll)
-    constexpr int UNROLL = (T == 2) ? kFold : (MINB >= 5 ? 8 : 4);
+    // (packed: 32 pair steps per fold, unrolled fully for two targets and by
+    // half for four)
+    constexpr int UNROLL = X2 ? (T == 2 ? kFold2 / 2 : kFold2 / 4) : (T == 2 ? kFold : (MINB >= 5 ? 8 : 4));
     constexpr int TB = kThreads * T;  // targets per block
     constexpr int TILE = TB;          // sources per tile
     extern __shared__ __align__(128) float4 smem32[];
-    float4 *sh_hi = smem32;                // [2][TILE]
+    float4 *sh_hi = smem32;                // [2][TILE] staging (bulk copies land here)
     float4 *sh_lo = smem32 + 2 * TILE;  // [2][TILE]
+    float4 *cp_hi = smem32 + 4 * TILE;  // X2: [TILE] pair-interleaved tile
+    float4 *cp_lo = smem32 + 5 * TILE;  // X2: [TILE]
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ int s_item, s_abort;
     const int tid = threadIdx.x;
@@ -197,6 +293,14 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
             tl[t][0] = l.x; tl[t][1] = l.y; tl[t][2] = l.z;
             tidx[t] = valid ? (part ? k : sd.n + k) : -1;
         }
+        float2 nth[T][3], ntl[T][3];  // X2: negated target words, both lanes
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nth[t][c] = make_float2(-th[t][c], -th[t][c]);
+                ntl[t][c] = make_float2(-tl[t][c], -tl[t][c]);
+            }
         float2 phi[T], g[T][3];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -238,17 +342,10 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
             parity[buf] ^= 1u;
             const long long s0 = (long long)(t0 + k) * TILE;
             const int cnt = (int)min((long long)TILE, Ns - s0);
-            const int cnt_pad = (cnt + kFold - 1) / kFold * kFold;
+            constexpr int FOLD = X2 ? kFold2 : kFold;
+            const int cnt_pad = (cnt + FOLD - 1) / FOLD * FOLD;
             float4 *bh = sh_hi + buf * TILE;
             float4 *bl = sh_lo + buf * TILE;
-            if (cnt_pad > cnt) {
-                for (int s = cnt + tid; s < cnt_pad; s += kThreads) {
-                    bh[s] = make_float4(kFar, -kFar, kFar, 0.f);
-                    bl[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            __syncthreads();
-            if (s_abort) break;
             const int skip = part ? ((s0 < tb_hi && s0 + cnt > tb_lo) ? 1 : 0) : (a.ext_skip_zero ? 2 : 0);
             int self_rel[T];
 #pragma unroll
@@ -262,6 +359,42 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
                 float gz = fmaxf(0.f, fmaxf(slo.z - bhi.z, blo.z - shi.z));
                 far = gx * gx + gy * gy + gz * gz >= a.far2;
             }
+            if constexpr (X2) {
+                // interleave the staged tile (low words only for near tiles),
+                // then hand the staging buffer back to the copy engine at once
+                interleave_pairs(bh, cp_hi, cnt, cnt_pad, make_float4(kFar, -kFar, kFar, 0.f), tid);
+                if (!far) interleave_pairs(bl, cp_lo, cnt, cnt_pad, make_float4(0.f, 0.f, 0.f, 0.f), tid);
+                __syncthreads();
+                if (s_abort) break;
+                if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
+                if (field) {
+                    if (far)
+                        tile32x2<T, UNROLL, true, 0, false>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                    else if (skip == 1)
+                        tile32x2<T, UNROLL, true, 1, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                    else if (skip == 2)
+                        tile32x2<T, UNROLL, true, 2, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                    else
+                        tile32x2<T, UNROLL, true, 0, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                } else {
+                    if (far)
+                        tile32x2<T, UNROLL, false, 0, false>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                    else if (skip == 2)
+                        tile32x2<T, UNROLL, false, 2, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                    else
+                        tile32x2<T, UNROLL, false, 0, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                }
+                __syncthreads();  // the interleaved tile is rewritten next
+                continue;
+            }
+            if (cnt_pad > cnt) {
+                for (int s = cnt + tid; s < cnt_pad; s += kThreads) {
+                    bh[s] = make_float4(kFar, -kFar, kFar, 0.f);
+                    bl[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
             if (field) {
                 if (far)
                     tile32<T, UNROLL, true, 0, false>(bh, bl, cnt_pad, th, tl, self_rel, phi, g);
@@ -478,18 +611,30 @@ __global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float
 
 }  // namespace
 
-int pair_targets_per_block(int precision, int variant)
+// FP32 kernel variants (the autotuner's candidates):
+//   4 = four targets per thread, >= 4 CTAs/SM      5 = four targets, >= 5 CTAs/SM
+//   2 = two targets, >= 6 CTAs/SM
+//  12 = two targets, packed two-source loop, >= 6 CTAs/SM
+//  13 = two targets, packed, >= 5 CTAs/SM         14 = four targets, packed, >= 3 CTAs/SM
+bool pair_variant_valid(int variant)
 {
-    return precision == HSMA_FP64 ? kTB64 : kThreads * (variant == 2 ? 2 : 4);
+    return variant == 4 || variant == 5 || variant == 2 || variant == 12 || variant == 13 || variant == 14;
 }
 
-// variant: 4 = four targets per thread at >= 4 CTAs/SM; 5 = four targets at
-// >= 5 CTAs/SM (fewer registers); 2 = two targets at >= 6 CTAs/SM.
+static int variant_targets(int variant) { return (variant == 2 || variant == 12 || variant == 13) ? 2 : 4; }
+static bool variant_packed(int variant) { return variant >= 12; }
+
+int pair_targets_per_block(int precision, int variant)
+{
+    return precision == HSMA_FP64 ? kTB64 : kThreads * variant_targets(variant);
+}
 
 static size_t pair_smem(int precision, int variant)
 {
-    return precision == HSMA_FP64 ? 2 * kTile64 * sizeof(double4_32a)
-                                  : 4 * (size_t)pair_targets_per_block(precision, variant) * sizeof(float4);
+    if (precision == HSMA_FP64) return 2 * kTile64 * sizeof(double4_32a);
+    // staging: 2 buffers x (hi, lo); packed variants add the interleaved (hi, lo)
+    const size_t tile = (size_t)pair_targets_per_block(precision, variant);
+    return (variant_packed(variant) ? 6 : 4) * tile * sizeof(float4);
 }
 
 template <class K>
@@ -505,9 +650,14 @@ int pair_max_ctas_per_sm(int precision, int variant)
 {
     const size_t sm = pair_smem(precision, variant);
     if (precision == HSMA_FP64) return occupancy_of(pair_fp64_kernel, sm);
-    if (variant == 2) return occupancy_of(pair_fp32_kernel<2, 6>, sm);
-    if (variant == 5) return occupancy_of(pair_fp32_kernel<4, 5>, sm);
-    return occupancy_of(pair_fp32_kernel<4, 4>, sm);
+    switch (variant) {
+    case 2: return occupancy_of(pair_fp32_kernel<2, 6, false>, sm);
+    case 5: return occupancy_of(pair_fp32_kernel<4, 5, false>, sm);
+    case 12: return occupancy_of(pair_fp32_kernel<2, 6, true>, sm);
+    case 13: return occupancy_of(pair_fp32_kernel<2, 5, true>, sm);
+    case 14: return occupancy_of(pair_fp32_kernel<4, 3, true>, sm);
+    default: return occupancy_of(pair_fp32_kernel<4, 4, false>, sm);
+    }
 }
 
 // The dynamic shared-memory attribute is set by pair_max_ctas_per_sm, which
@@ -517,14 +667,18 @@ int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStr
 {
     if (a.total_items <= 0) return HSMA_OK;
     const size_t sm = pair_smem(precision, variant);
-    if (precision == HSMA_FP64)
+    if (precision == HSMA_FP64) {
         pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
-    else if (variant == 2)
-        pair_fp32_kernel<2, 6><<<grid, kThreads, sm, st>>>(a);
-    else if (variant == 5)
-        pair_fp32_kernel<4, 5><<<grid, kThreads, sm, st>>>(a);
-    else
-        pair_fp32_kernel<4, 4><<<grid, kThreads, sm, st>>>(a);
+    } else {
+        switch (variant) {
+        case 2: pair_fp32_kernel<2, 6, false><<<grid, kThreads, sm, st>>>(a); break;
+        case 5: pair_fp32_kernel<4, 5, false><<<grid, kThreads, sm, st>>>(a); break;
+        case 12: pair_fp32_kernel<2, 6, true><<<grid, kThreads, sm, st>>>(a); break;
+        case 13: pair_fp32_kernel<2, 5, true><<<grid, kThreads, sm, st>>>(a); break;
+        case 14: pair_fp32_kernel<4, 3, true><<<grid, kThreads, sm, st>>>(a); break;
+        default: pair_fp32_kernel<4, 4, false><<<grid, kThreads, sm, st>>>(a); break;
+        }
+    }
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

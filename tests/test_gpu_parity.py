@@ -187,6 +187,41 @@ def test_ragged_sizes_fp64(n):
         assert_within(errors(F.cpu().numpy(), ref["forces"], U, ref["energy"]), "fp32", f"n={n}")
 
 
+# every blocking of the FP32 pair kernel the autotuner may pick
+PAIR_VARIANTS = [4, 5, 2, 12, 13, 14]
+
+
+@pytest.mark.parametrize("variant", PAIR_VARIANTS)
+def test_pair_variants_against_oracle(small_periodic, grounded_small, variant):
+    """Each FP32 pair-kernel variant (scalar and packed, two and four targets
+    per thread) at a fine and a coarse work split, periodic and grounded,
+    against the oracle; plus a ragged size whose last tile and block are
+    partial."""
+    xyz, q, ref, _ = small_periodic
+    w = I.SMALL_PERIODIC
+    for ips in (8, 48):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+            plan.set_tuning(variant, ips)
+            U, F, pot, ns = plan.energy_forces(*to_dev(xyz, q), potentials=True)
+            assert ns == ref["n_inset"]
+            e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+            assert_within(e, "fp32", f"periodic variant {variant} items {ips}")
+    wg, xg, qg, refg = grounded_small
+    with hs().Plan(wg.box, wg.bc, wg.p, wg.R, wg.Q, wg.Kmon, precision="fp32") as plan:
+        plan.set_tuning(variant, 16)
+        U, F, pot, ns = plan.energy_forces(*to_dev(xg, qg), potentials=True)
+        assert ns == refg["n_inset"]
+        e = errors(F.cpu().numpy(), refg["forces"], U, refg["energy"], pot.cpu().numpy(), refg["pot"])
+        assert_within(e, "fp32", f"grounded variant {variant}")
+    wt = I.Workload("tiny", (1.0, 1.0, 1.0), I.PERIODIC, 6, 1.5, 600, 200)
+    xt, qt = I.random_neutral(514, wt.box, seed_offset=30 + 513)
+    reft, _ = oracle_run(xt, qt, wt)
+    with hs().Plan(wt.box, wt.bc, wt.p, wt.R, wt.Q, wt.Kmon, precision="fp32") as plan:
+        plan.set_tuning(variant, 24)
+        U, F, _, _ = plan.energy_forces(*to_dev(xt, qt))
+        assert_within(errors(F.cpu().numpy(), reft["forces"], U, reft["energy"]), "fp32", f"n=514 variant {variant}")
+
+
 def test_error_codes():
     hsma = hs()
     w = I.SMALL_PERIODIC
@@ -257,17 +292,25 @@ def test_large_periodic_sampled_full_size():
     ref, _ = oracle_run(xyz, q, w, sample=sample, nthreads=16)
     dx, dq = to_dev(xyz, q)
     res = {}
-    for prec in ("fp32", "fp64"):
+    # FP64 and every FP32 pair-kernel variant (the benchmark times the one the
+    # autotuner picks, with 48 items per slot)
+    runs = [("fp64", None)] + [("fp32", v) for v in PAIR_VARIANTS]
+    for prec, variant in runs:
         with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            if variant is not None:
+                plan.set_tuning(variant, 48)
             U, F, pot, ns = plan.energy_forces(dx, dq, potentials=True)
             assert ns == ref["n_inset"]
-            res[prec] = (U, F.cpu().numpy(), pot.cpu().numpy())
-            e = errors(res[prec][1][sample], ref["forces"], None, None, res[prec][2][sample], ref["pot"])
+            res[(prec, variant)] = (U, F.cpu().numpy(), pot.cpu().numpy())
+            r = res[(prec, variant)]
+            e = errors(r[1][sample], ref["forces"], None, None, r[2][sample], ref["pot"])
             tol = TOL[prec]
-            assert e["force_rms"] <= tol["force_rms"] and e["pot_rms"] <= tol["pot_rms"], (prec, e)
-    U32, U64 = res["fp32"][0], res["fp64"][0]
-    assert abs(U32 - U64) <= 1e-6 * abs(U64)
-    assert rms(res["fp32"][1] - res["fp64"][1]) <= 1e-5 * rms(res["fp64"][1])
+            assert e["force_rms"] <= tol["force_rms"] and e["pot_rms"] <= tol["pot_rms"], (prec, variant, e)
+    U64, F64 = res[("fp64", None)][0], res[("fp64", None)][1]
+    for v in PAIR_VARIANTS:
+        U32, F32 = res[("fp32", v)][0], res[("fp32", v)][1]
+        assert abs(U32 - U64) <= 1e-6 * abs(U64), v
+        assert rms(F32 - F64) <= 1e-5 * rms(F64), v
 
 
 @pytest.mark.slow

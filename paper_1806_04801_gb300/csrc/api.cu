@@ -74,6 +74,7 @@ struct Workspace {
     SysDesc *sys = nullptr;
     float *tc_work = nullptr;
     long long *idx64 = nullptr;                     // target sharding: caller indices of a slice
+    double4_32a *cen = nullptr;                     // in-set scratch: centred particles, spatial order
 };
 
 struct BatchShape {
@@ -364,6 +365,7 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys))
                                                   : nullptr;
     w->idx64 = c.take<long long>(sh.n_total);
+    w->cen = c.take<double4_32a>(sh.n_total);
     return align_up(c.off, 256);
 }
 
@@ -460,6 +462,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     ia.src_lo = w.src_lo;
     ia.src64 = w.src64;
     ia.status = w.status;
+    ia.cen = w.cen;
     if ((rc = launch_inset(ia, st))) return rc;
     const int TB = pair_targets_per_block(prec, sh.variant);
     if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
@@ -804,6 +807,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
     ia.src_lo = w.src_lo;
     ia.src64 = w.src64;
     ia.status = w.status;
+    ia.cen = w.cen;
     if ((rc = launch_inset(ia, st))) return rc;
 
     const long long cnt = t_hi - t_lo;
@@ -1354,9 +1358,9 @@ int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_p
     const hsma_tuning value0 = pl->tune_value;
     std::vector<double> energies(nsys);
     std::vector<hsma_tuning> cands;
-    const int variants[6] = {4, 5, 2, 12, 13, 14};
+    const int variants[8] = {4, 5, 2, 12, 13, 14, 15, 16};
     const int items[4] = {8, 16, 24, 48};
-    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 6); ++v)
+    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 8); ++v)
         for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
     hsma_tuning win{4, 24, 1e300};
     int rc = HSMA_OK;

@@ -72,6 +72,18 @@ __device__ __forceinline__ float2 df_add(float2 acc, float x)
     return make_float2(s, __fadd_rn(acc.y, e));
 }
 
+// Double-float sum of two double-float values (TwoSum of the high words, low
+// words added to the error term, renormalised): ~2^-44 relative.
+__device__ __forceinline__ float2 df_add_df(float2 a, float2 b)
+{
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
 // Reciprocal square root on the special-function unit.
 __device__ __forceinline__ float rsqrt_sfu(float x)
 {
@@ -175,6 +187,57 @@ __device__ __forceinline__ double block_sum(double v, double *scratch /* >= 32 *
     return r;
 }
 
+// Exclusive prefix sum of h[0, total) in place by one block (blockDim a
+// multiple of 32, <= 1024); returns the sum of all entries.  Each thread
+// scans kPer consecutive entries per round, so a round covers
+// kPer * blockDim entries with two block barriers.
+__device__ __forceinline__ long long block_scan_inplace(int *h, long long total, int *wsum /* [32] */,
+                                                        long long *carry_s)
+{
+    constexpr int kPer = 8;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long carry = 0;
+    for (long long base = 0; base < total; base += (long long)blockDim.x * kPer) {
+        const long long t0 = base + (long long)threadIdx.x * kPer;
+        int v[kPer];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            v[k] = (t0 + k < total) ? h[t0 + k] : 0;
+            sum += v[k];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < nw) ? wsum[lane] : 0;
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            wsum[lane] = wi - w;  // exclusive prefix of the warp sums
+            if (lane == 31) *carry_s = carry + wi;
+        }
+        __syncthreads();
+        long long e = carry + wsum[wid] + incl - sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (t0 + k < total) h[t0 + k] = (int)e;
+            e += v[k];
+        }
+        carry = *carry_s;
+        __syncthreads();  // wsum and carry_s are rewritten next round
+    }
+    return carry;
+}
+
 // ------------------------------------------------ kernel launch interfaces
 // (defined in the .cu files; all enqueue on `st` and return HSMA_OK or a code)
 
@@ -231,6 +294,7 @@ struct InsetArgs {
     float4 *src_lo;
     double4_32a *src64;
     int *status;
+    double4_32a *cen;       // [n] scratch: centred (x, y, z, q) in spatial order
 };
 int launch_inset(const InsetArgs &a, cudaStream_t st);
 

@@ -80,9 +80,15 @@ __global__ void surface_charges_kernel(int ndir, int Nb, const double *Bq, const
     }
 }
 
-constexpr int kSurfThreads = 128;
+// A block of kSurfThreads = kSurfSplit x kSurfGroup threads covers kSurfTB
+// particles (kSurfT per thread); the kSurfSplit thread groups take every
+// kSurfSplit-th direction of each staged tile (more warps per SM for the
+// same work), and their partial sums are added in group order at the end.
+constexpr int kSurfThreads = 256;
+constexpr int kSurfSplit = 4;
+constexpr int kSurfGroup = kSurfThreads / kSurfSplit;
 constexpr int kSurfT = 2;
-constexpr int kSurfTB = kSurfThreads * kSurfT;
+constexpr int kSurfTB = kSurfGroup * kSurfT;
 constexpr int kSurfTile = 256;
 
 __device__ __forceinline__ int find_sys_surf(const SysDesc *sys, int nsys, int item)
@@ -105,20 +111,23 @@ __device__ __forceinline__ int find_sys_surf(const SysDesc *sys, int nsys, int i
 //   its field:    (p/dr)((d + h u)/A^3 - (d - h u)/B^3)
 //                 = p [ -2 a (A^2 + A B + B^2) / ((A + B) A^3 B^3) d
 //                       + (u/2)(1/A^3 + 1/B^3) ]
-__global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
+__global__ void __launch_bounds__(kSurfThreads, 4) surface_pairs_fp32_kernel(
     const SysDesc *sys, int nsys, const float4 *src_hi, const float4 *src_lo, int ndir, const double4_32a *dirs,
     const double2 *img, float Rs, float h, double *phi_out, double *e_out)
 {
     __shared__ float4 su[kSurfTile];   // (u_x, u_y, u_z, Q_sigma)
     __shared__ float sp[kSurfTile];    // p
+    __shared__ float2 red[kSurfSplit - 1][kSurfT][4][kSurfGroup];  // partial sums of groups 1..
     const int s = find_sys_surf(sys, nsys, blockIdx.x);
     const SysDesc sd = sys[s];
     const int blk = blockIdx.x - sd.surf_off;
+    const int gl = threadIdx.x % kSurfGroup;  // particle lane
+    const int grp = threadIdx.x / kSurfGroup;  // direction group (uniform per warp)
     float rx[kSurfT], ry[kSurfT], rz[kSurfT];
     long long idx[kSurfT];
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
-        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurfGroup + gl;
         const bool ok = i < sd.sp_lo + sd.sp_n;
         idx[t] = ok ? i : -1;
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
@@ -151,7 +160,7 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
         float pa[kSurfT], ea[kSurfT][3];
 #pragma unroll
         for (int t = 0; t < kSurfT; ++t) pa[t] = ea[t][0] = ea[t][1] = ea[t][2] = 0.f;
-        for (int j = 0; j < cnt; ++j) {
+        for (int j = grp; j < cnt; j += kSurfSplit) {
             const float4 u = su[j];
             const float p = sp[j];
 #pragma unroll
@@ -189,8 +198,27 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
             e[t][2] = df_add(e[t][2], ea[t][2]);
         }
     }
+    // add the groups' partial sums in group order
+    if (grp > 0) {
+#pragma unroll
+        for (int t = 0; t < kSurfT; ++t) {
+            red[grp - 1][t][0][gl] = phi[t];
+            red[grp - 1][t][1][gl] = e[t][0];
+            red[grp - 1][t][2][gl] = e[t][1];
+            red[grp - 1][t][3][gl] = e[t][2];
+        }
+    }
+    __syncthreads();
+    if (grp > 0) return;
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
+#pragma unroll
+        for (int g2 = 0; g2 < kSurfSplit - 1; ++g2) {
+            phi[t] = df_add_df(phi[t], red[g2][t][0][gl]);
+            e[t][0] = df_add_df(e[t][0], red[g2][t][1][gl]);
+            e[t][1] = df_add_df(e[t][1], red[g2][t][2][gl]);
+            e[t][2] = df_add_df(e[t][2], red[g2][t][3][gl]);
+        }
         if (idx[t] < 0) continue;
         long long o = sd.part_off + idx[t];
         phi_out[o] = (double)phi[t].x + (double)phi[t].y;
@@ -200,8 +228,10 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp32_kernel(
     }
 }
 
-// FP64 form: the three point images of each direction summed literally.
-__global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
+// FP64 form: the three point images of each direction summed literally; one
+// particle per thread, kSurfTB per block (the FP32 kernel's block size).
+constexpr int kSurf64Threads = kSurfTB;
+__global__ void __launch_bounds__(kSurf64Threads) surface_pairs_fp64_kernel(
     const SysDesc *sys, int nsys, const double4_32a *src64, int ndir, const double4_32a *dirs, const double2 *img,
     double Rs, double dr, double *phi_out, double *e_out)
 {
@@ -210,11 +240,12 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
     const int s = find_sys_surf(sys, nsys, blockIdx.x);
     const SysDesc sd = sys[s];
     const int blk = blockIdx.x - sd.surf_off;
-    double r[kSurfT][3];
-    long long idx[kSurfT];
+    constexpr int T = 1;
+    double r[T][3];
+    long long idx[T];
 #pragma unroll
-    for (int t = 0; t < kSurfT; ++t) {
-        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurfThreads + threadIdx.x;
+    for (int t = 0; t < T; ++t) {
+        long long i = sd.sp_lo + (long long)blk * kSurfTB + t * kSurf64Threads + threadIdx.x;
         const bool ok = i < sd.sp_lo + sd.sp_n;
         idx[t] = ok ? i : -1;
         double4_32a a = make_double4_32a(0, 0, 0, 0);
@@ -223,15 +254,15 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
         r[t][1] = a.y;
         r[t][2] = a.z;
     }
-    double phi[kSurfT], e[kSurfT][3];
+    double phi[T], e[T][3];
 #pragma unroll
-    for (int t = 0; t < kSurfT; ++t) phi[t] = e[t][0] = e[t][1] = e[t][2] = 0.0;
+    for (int t = 0; t < T; ++t) phi[t] = e[t][0] = e[t][1] = e[t][2] = 0.0;
     const double2 *im = img + (long long)s * ndir;
     const double Rin = Rs - 0.5 * dr, Rout = Rs + 0.5 * dr;
     for (int d0 = 0; d0 < ndir; d0 += kSurfTile) {
         int cnt = min(kSurfTile, ndir - d0);
         __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += kSurfThreads) {
+        for (int j = threadIdx.x; j < cnt; j += kSurf64Threads) {
             double4_32a u = dirs[d0 + j];
             double2 c = im[d0 + j];
             su[j] = make_double4_32a(u.x, u.y, u.z, c.x);
@@ -244,7 +275,7 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
             const double R3[3] = {Rs, Rin, Rout};
             const double Q3[3] = {u.w, pd, -pd};
 #pragma unroll
-            for (int t = 0; t < kSurfT; ++t) {
+            for (int t = 0; t < T; ++t) {
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
                     double dx = r[t][0] - R3[m] * u.x;
@@ -262,7 +293,7 @@ __global__ void __launch_bounds__(kSurfThreads) surface_pairs_fp64_kernel(
         }
     }
 #pragma unroll
-    for (int t = 0; t < kSurfT; ++t) {
+    for (int t = 0; t < T; ++t) {
         if (idx[t] < 0) continue;
         long long o = sd.part_off + idx[t];
         phi_out[o] = phi[t];
@@ -357,7 +388,7 @@ int launch_surface_pairs(const SysDesc *sys, int nsys, int total_items, const lo
     (void)ns;
     if (total_items <= 0) return HSMA_OK;
     if (precision == HSMA_FP64)
-        surface_pairs_fp64_kernel<<<total_items, kSurfThreads, 0, st>>>(sys, nsys, src64, ndir, dirs, img, Rs, dr,
+        surface_pairs_fp64_kernel<<<total_items, kSurf64Threads, 0, st>>>(sys, nsys, src64, ndir, dirs, img, Rs, dr,
                                                                          phi_out, e_out);
     else
         surface_pairs_fp32_kernel<<<total_items, kSurfThreads, 0, st>>>(

@@ -3,10 +3,12 @@
 // (r_j + k∘L) or, for the grounded box, Eq. "diel" at gamma = -1
 // ((-1)^k ∘ r_j + k∘L with charge (-1)^{|k|} q_j).
 //
-// Three kernels give a deterministic compacted order -- shift k = 0 first (so
+// Four kernels give a deterministic compacted order -- shift k = 0 first (so
 // in-set slot i of a system is its i-th particle in spatial order, perm[i]),
 // then the other shifts in the order of the shift table, each over the
 // particles in spatial order:
+//   centre  : per particle (spatial order) the centred, wrapped position and
+//             charge, once (the FP64 wrap is not repeated for every shift);
 //   count   : per (system, shift, block of particles) the number of hits;
 //   scan    : per system, exclusive prefix over (shift, block) + totals, and
 //             the neutrality check of periodic systems;
@@ -68,6 +70,29 @@ __device__ __forceinline__ bool image_of(const Centred &c, int4 s, const Geometr
     return x * x + y * y + z * z < g.Rs * g.Rs;
 }
 
+__global__ void __launch_bounds__(kInsetThreads) inset_centre_kernel(InsetArgs a)
+{
+    int sys_i = blockIdx.y;
+    const SysDesc sd = a.sys[sys_i];
+    long long j = (long long)blockIdx.x * kInsetThreads + threadIdx.x;
+    if (blockIdx.x >= sd.nblk || j >= sd.n) return;
+    Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
+    if (!c.ok) atomicOr(&a.status[sys_i], ST_OUT_OF_BOX);
+    a.cen[sd.part_off + j] = make_double4_32a(c.x, c.y, c.z, c.q);
+}
+
+__device__ __forceinline__ Centred centred_at(const InsetArgs &a, const SysDesc &sd, long long j)
+{
+    const double4_32a v = a.cen[sd.part_off + j];
+    Centred c;
+    c.x = v.x;
+    c.y = v.y;
+    c.z = v.z;
+    c.q = v.w;
+    c.ok = true;
+    return c;
+}
+
 __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
 {
     int sys_i = blockIdx.z;
@@ -78,8 +103,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
     long long j = (long long)blk * kInsetThreads + threadIdx.x;
     int hit = 0;
     if (j < sd.n) {
-        Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
-        if (sh == 0 && !c.ok) atomicOr(&a.status[sys_i], ST_OUT_OF_BOX);
+        Centred c = centred_at(a, sd, j);
         double x, y, z, q;
         hit = image_of(c, a.shifts[sh], a.g, x, y, z, q) ? 1 : 0;
     }
@@ -90,42 +114,12 @@ __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
 __global__ void __launch_bounds__(1024) inset_scan_kernel(InsetArgs a)
 {
     __shared__ int wsum[32];
-    __shared__ int carry;
+    __shared__ long long carry;
     __shared__ double red[32];
     int sys_i = blockIdx.x;
     const SysDesc sd = a.sys[sys_i];
-    long long total = (long long)a.n_shifts * sd.nblk;
-    int *cnt = a.counts + sd.cnt_off;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long base = 0; base < total; base += blockDim.x) {
-        long long t = base + threadIdx.x;
-        int v = (t < total) ? cnt[t] : 0;
-        int incl = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int w = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-            int wi = w;
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += u;
-            }
-            wsum[lane] = wi - w;  // exclusive prefix of warp sums
-        }
-        __syncthreads();
-        int excl = carry + wsum[wid] + incl - v;
-        if (t < total) cnt[t] = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) a.ns[sys_i] = carry;
+    const long long total = block_scan_inplace(a.counts + sd.cnt_off, (long long)a.n_shifts * sd.nblk, wsum, &carry);
+    if (threadIdx.x == 0) a.ns[sys_i] = total;
     // neutrality of periodic systems: |sum q| <= 1e-12 sum |q| (deterministic order)
     double s = 0.0, sa = 0.0;
     for (long long j = threadIdx.x; j < sd.n; j += blockDim.x) {
@@ -151,7 +145,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_scatter_kernel(InsetArgs 
     bool hit = false;
     double x = 0, y = 0, z = 0, q = 0;
     if (j < sd.n) {
-        Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
+        Centred c = centred_at(a, sd, j);
         hit = image_of(c, a.shifts[sh], a.g, x, y, z, q);
     }
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -179,6 +173,8 @@ __global__ void __launch_bounds__(kInsetThreads) inset_scatter_kernel(InsetArgs 
 int launch_inset(const InsetArgs &a, cudaStream_t st)
 {
     dim3 grid(a.nblk_max, a.n_shifts, a.nsys);
+    inset_centre_kernel<<<dim3(a.nblk_max, a.nsys), kInsetThreads, 0, st>>>(a);
+    HSMA_LAUNCHED();
     inset_count_kernel<<<grid, kInsetThreads, 0, st>>>(a);
     HSMA_LAUNCHED();
     inset_scan_kernel<<<a.nsys, 1024, 0, st>>>(a);

@@ -34,6 +34,7 @@ constexpr int kTB64 = kThreads * kT64;
 constexpr int kTile64 = 256;
 constexpr int kFold = 32;               // potential fold interval (sources)
 constexpr int kFold2 = 64;              // packed loop: 32 sources per lane
+constexpr bool kCpDouble = true;        // mode 1: two interleaved buffers, one barrier per tile
 constexpr float kFar = 1.0e4f;          // position of zero-charge padding sources
 
 struct Item {
@@ -130,11 +131,14 @@ __device__ __forceinline__ void tile32(const float4 *__restrict__ sh, const floa
 // that the potential takes q/r with one fused multiply-add.  A lane sums 32
 // sources of a 64-source fold interval (even and odd slots), the same FP32
 // run length as tile32; the two lane sums are added and folded with one
-// TwoSum.
-template <int T, int UNROLL, bool FIELD, int SKIP, bool SPLIT>
-__device__ __forceinline__ void tile32x2(const float4 *__restrict__ ph, const float4 *__restrict__ pl, int cnt_pad,
+// TwoSum.  SACC: the double-float accumulators live in shared memory
+// (acc[j * kThreads], j = t for the potential of target t, T + 3t + c for
+// field component c) instead of phi / g, which frees their registers.
+template <int T, int UNROLL, bool FIELD, int SKIP, bool SPLIT, bool SACC>
+__device__ __forceinline__ void tile32x2(const float4 *ph, const float4 *pl, int cnt_pad,
                                          const float2 (&nth)[T][3], const float2 (&ntl)[T][3],
-                                         const int (&self_rel)[T], float2 (&phi)[T], float2 (&g)[T][3])
+                                         const int (&self_rel)[T], float2 (&phi)[T], float2 (&g)[T][3],
+                                         float2 *acc)
 {
     float2 ga[T][3];
 #pragma unroll
@@ -187,20 +191,34 @@ __device__ __forceinline__ void tile32x2(const float4 *__restrict__ ph, const fl
             }
         }
 #pragma unroll
-        for (int t = 0; t < T; ++t) phi[t] = df_add(phi[t], pa[t].x + pa[t].y);
+        for (int t = 0; t < T; ++t) {
+            if (SACC)
+                acc[t * kThreads] = df_add(acc[t * kThreads], pa[t].x + pa[t].y);
+            else
+                phi[t] = df_add(phi[t], pa[t].x + pa[t].y);
+        }
     }
     if (FIELD) {
 #pragma unroll
         for (int t = 0; t < T; ++t)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) g[t][c] = df_add(g[t][c], ga[t][c].x + ga[t][c].y);
+            for (int c = 0; c < 3; ++c) {
+                if (SACC) {
+                    float2 &e = acc[(T + 3 * t + c) * kThreads];
+                    e = df_add(e, ga[t][c].x + ga[t][c].y);
+                } else {
+                    g[t][c] = df_add(g[t][c], ga[t][c].x + ga[t][c].y);
+                }
+            }
     }
 }
 
 // Pair-interleave a staged tile (one float4 per source) into the layout of
-// tile32x2; slots cnt..cnt_pad-1 become the padding source `pad`.
-__device__ __forceinline__ void interleave_pairs(const float4 *__restrict__ src, float4 *__restrict__ dst, int cnt,
-                                                 int cnt_pad, float4 pad, int tid)
+// tile32x2; slots cnt..cnt_pad-1 become the padding source `pad`.  dst may be
+// src: each thread reads both sources of a pair before it rewrites the same
+// 32 bytes.
+__device__ __forceinline__ void interleave_pairs(const float4 *src, float4 *dst, int cnt, int cnt_pad, float4 pad,
+                                                 int tid)
 {
     for (int p = tid; 2 * p < cnt_pad; p += kThreads) {
         const int i = 2 * p;
@@ -211,13 +229,17 @@ __device__ __forceinline__ void interleave_pairs(const float4 *__restrict__ src,
     }
 }
 
-// MINB: CTAs per SM the register allocation must allow (4 or 5 for T = 4,
-// 5 or 6 for T = 2); X2: packed two-source loop (tile32x2) on a
-// pair-interleaved copy of each staged tile.  The autotuner picks among these
-// variants.
-template <int T, int MINB, bool X2>
+// MINB: CTAs per SM the register allocation must allow.  MODE 0: scalar loop
+// (tile32); 1: packed two-source loop (tile32x2) on a pair-interleaved copy of
+// each staged tile in a third buffer, the staging buffer refilled at once;
+// 2: packed loop on the staging buffer interleaved in place, double-float
+// accumulators in shared memory (fewer registers, refill after the tile).
+// The autotuner picks among these variants.
+template <int T, int MINB, int MODE>
 __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
 {
+    constexpr bool X2 = MODE != 0;
+    constexpr bool SACC = MODE == 2;
     // source-loop unrolling per variant (measured: 4 targets at 4 CTAs/SM
     // prefers 4, at 5 CTAs/SM 8, two targets a full unroll)
     // (packed: 32 pair steps per fold, unrolled fully for two targets and by
@@ -228,8 +250,10 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
     extern __shared__ __align__(128) float4 smem32[];
     float4 *sh_hi = smem32;                // [2][TILE] staging (bulk copies land here)
     float4 *sh_lo = smem32 + 2 * TILE;  // [2][TILE]
-    float4 *cp_hi = smem32 + 4 * TILE;  // X2: [TILE] pair-interleaved tile
-    float4 *cp_lo = smem32 + 5 * TILE;  // X2: [TILE]
+    float4 *cp_hi = smem32 + 4 * TILE;  // MODE 1: [1 or 2][TILE] pair-interleaved tile
+    float4 *cp_lo = smem32 + (kCpDouble ? 6 : 5) * TILE;  // MODE 1: [1 or 2][TILE]
+    // MODE 2: [4T][kThreads] double-float accumulators, this thread's column
+    float2 *acc = reinterpret_cast<float2 *>(smem32 + 4 * TILE) + threadIdx.x;
     __shared__ __align__(8) uint64_t bar[3];
     __shared__ int s_item, s_abort;
     const int tid = threadIdx.x;
@@ -307,6 +331,10 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
             phi[t] = make_float2(0.f, 0.f);
             g[t][0] = g[t][1] = g[t][2] = make_float2(0.f, 0.f);
         }
+        if constexpr (SACC) {
+#pragma unroll
+            for (int j = 0; j < 4 * T; ++j) acc[j * kThreads] = make_float2(0.f, 0.f);
+        }
 
         // box of this block's targets (= in-set tile `tb`, its particles), for
         // the near/far decision per source tile
@@ -359,32 +387,65 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
                 float gz = fmaxf(0.f, fmaxf(slo.z - bhi.z, blo.z - shi.z));
                 far = gx * gx + gy * gy + gz * gz >= a.far2;
             }
-            if constexpr (X2) {
+            if constexpr (MODE == 2) {
+                // interleave the staged tile in place (low words only for near
+                // tiles); the buffer is refilled once the tile is done
+                interleave_pairs(bh, bh, cnt, cnt_pad, make_float4(kFar, -kFar, kFar, 0.f), tid);
+                if (!far) interleave_pairs(bl, bl, cnt, cnt_pad, make_float4(0.f, 0.f, 0.f, 0.f), tid);
+                fence_proxy_async_smem();  // these writes precede the buffer's next bulk copy
+                __syncthreads();
+                if (s_abort) break;
+                if (field) {
+                    if (far)
+                        tile32x2<T, UNROLL, true, 0, false, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                    else if (skip == 1)
+                        tile32x2<T, UNROLL, true, 1, true, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                    else if (skip == 2)
+                        tile32x2<T, UNROLL, true, 2, true, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                    else
+                        tile32x2<T, UNROLL, true, 0, true, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                } else {
+                    if (far)
+                        tile32x2<T, UNROLL, false, 0, false, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                    else if (skip == 2)
+                        tile32x2<T, UNROLL, false, 2, true, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                    else
+                        tile32x2<T, UNROLL, false, 0, true, true>(bh, bl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
+                }
+                __syncthreads();
+                if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
+                continue;
+            }
+            if constexpr (MODE == 1) {
                 // interleave the staged tile (low words only for near tiles),
                 // then hand the staging buffer back to the copy engine at once
-                interleave_pairs(bh, cp_hi, cnt, cnt_pad, make_float4(kFar, -kFar, kFar, 0.f), tid);
-                if (!far) interleave_pairs(bl, cp_lo, cnt, cnt_pad, make_float4(0.f, 0.f, 0.f, 0.f), tid);
+                float4 *ch = cp_hi + (kCpDouble ? buf * TILE : 0);
+                float4 *cl = cp_lo + (kCpDouble ? buf * TILE : 0);
+                interleave_pairs(bh, ch, cnt, cnt_pad, make_float4(kFar, -kFar, kFar, 0.f), tid);
+                if (!far) interleave_pairs(bl, cl, cnt, cnt_pad, make_float4(0.f, 0.f, 0.f, 0.f), tid);
                 __syncthreads();
                 if (s_abort) break;
                 if (tid == 0 && k + 2 < ntile) issue(k + 2, buf);
                 if (field) {
                     if (far)
-                        tile32x2<T, UNROLL, true, 0, false>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, true, 0, false, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                     else if (skip == 1)
-                        tile32x2<T, UNROLL, true, 1, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, true, 1, true, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                     else if (skip == 2)
-                        tile32x2<T, UNROLL, true, 2, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, true, 2, true, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                     else
-                        tile32x2<T, UNROLL, true, 0, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, true, 0, true, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                 } else {
                     if (far)
-                        tile32x2<T, UNROLL, false, 0, false>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, false, 0, false, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                     else if (skip == 2)
-                        tile32x2<T, UNROLL, false, 2, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, false, 2, true, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                     else
-                        tile32x2<T, UNROLL, false, 0, true>(cp_hi, cp_lo, cnt_pad, nth, ntl, self_rel, phi, g);
+                        tile32x2<T, UNROLL, false, 0, true, false>(ch, cl, cnt_pad, nth, ntl, self_rel, phi, g, acc);
                 }
-                __syncthreads();  // the interleaved tile is rewritten next
+                // one interleaved buffer: it is rewritten next, wait for every
+                // warp; two: the barrier after the next interleave suffices
+                if (!kCpDouble) __syncthreads();
                 continue;
             }
             if (cnt_pad > cnt) {
@@ -392,6 +453,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
                     bh[s] = make_float4(kFar, -kFar, kFar, 0.f);
                     bl[s] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+                fence_proxy_async_smem();  // these writes precede the buffer's next bulk copy
             }
             __syncthreads();
             if (s_abort) break;
@@ -421,6 +483,14 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
             break;
         }
         float4 *rec = a.partials + 2 * (sd.partial_off + (long long)it.chunk * ntgt);
+        if constexpr (SACC) {
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                phi[t] = acc[t * kThreads];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g[t][c] = acc[(T + 3 * t + c) * kThreads];
+            }
+        }
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             if (tidx[t] < 0) continue;
@@ -571,7 +641,12 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp64_kernel(PairArgs a)
     }
 }
 
-// Sum the chunk partials of every target in chunk order (deterministic).
+// Sum the chunk partials of every target (deterministic: four running sums
+// over the chunks c = 0, 1, 2, 3 mod 4, each in chunk order, then added in a
+// fixed order; the four independent streams keep four loads per thread in
+// flight).  FP32 records are double-float values and are summed in
+// double-float arithmetic on the FP32 pipe (FP64 issue is far slower on this
+// part); the total is converted to FP64 once.
 // phi_tgt[tgt_off + t] = potential, e_part[3 (tgt_off + t) + a] = field
 // E = -sum q (y - x)/r^3.
 __global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float4 *partials, int precision,
@@ -581,48 +656,103 @@ __global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float
     long long ntgt = sd.n + n_ext;
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntgt) return;
-    double p = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    const int nc = sd.nchunks;
+    const long long o = sd.tgt_off + t;
     if (precision == HSMA_FP64) {
-        const double4_32a *rec = reinterpret_cast<const double4_32a *>(partials) + sd.partial_off;
-        for (int c = 0; c < sd.nchunks; ++c) {
-            double4_32a r = rec[(long long)c * ntgt + t];
-            p += r.x;
-            gx += r.y;
-            gy += r.z;
-            gz += r.w;
+        double p[4] = {0.0, 0.0, 0.0, 0.0}, gx[4] = {0.0, 0.0, 0.0, 0.0}, gy[4] = {0.0, 0.0, 0.0, 0.0},
+               gz[4] = {0.0, 0.0, 0.0, 0.0};
+        const double4_32a *rec = reinterpret_cast<const double4_32a *>(partials) + sd.partial_off + t;
+        int c = 0;
+        for (; c + 4 <= nc; c += 4) {
+            double4_32a r[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) r[j] = rec[(long long)(c + j) * ntgt];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                p[j] += r[j].x;
+                gx[j] += r[j].y;
+                gy[j] += r[j].z;
+                gz[j] += r[j].w;
+            }
         }
-    } else {
-        const float4 *rec = partials + 2 * sd.partial_off;
-        for (int c = 0; c < sd.nchunks; ++c) {
-            float4 r0 = rec[2 * ((long long)c * ntgt + t)];
-            float4 r1 = rec[2 * ((long long)c * ntgt + t) + 1];
-            p += (double)r0.x + (double)r0.y;
-            gx += (double)r0.z + (double)r0.w;
-            gy += (double)r1.x + (double)r1.y;
-            gz += (double)r1.z + (double)r1.w;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (c + j >= nc) break;
+            double4_32a r = rec[(long long)(c + j) * ntgt];
+            p[j] += r.x;
+            gx[j] += r.y;
+            gy[j] += r.z;
+            gz[j] += r.w;
+        }
+        phi_tgt[o] = (p[0] + p[1]) + (p[2] + p[3]);
+        e_part[3 * o] = -((gx[0] + gx[1]) + (gx[2] + gx[3]));
+        e_part[3 * o + 1] = -((gy[0] + gy[1]) + (gy[2] + gy[3]));
+        e_part[3 * o + 2] = -((gz[0] + gz[1]) + (gz[2] + gz[3]));
+        return;
+    }
+    const float2 z2 = make_float2(0.f, 0.f);
+    float2 p[4] = {z2, z2, z2, z2}, gx[4] = {z2, z2, z2, z2}, gy[4] = {z2, z2, z2, z2}, gz[4] = {z2, z2, z2, z2};
+    const float4 *rec = partials + 2 * (sd.partial_off + t);
+    int c = 0;
+    for (; c + 4 <= nc; c += 4) {
+        float4 r0[4], r1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            r0[j] = rec[2 * (long long)(c + j) * ntgt];
+            r1[j] = rec[2 * (long long)(c + j) * ntgt + 1];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            p[j] = df_add_df(p[j], make_float2(r0[j].x, r0[j].y));
+            gx[j] = df_add_df(gx[j], make_float2(r0[j].z, r0[j].w));
+            gy[j] = df_add_df(gy[j], make_float2(r1[j].x, r1[j].y));
+            gz[j] = df_add_df(gz[j], make_float2(r1[j].z, r1[j].w));
         }
     }
-    long long o = sd.tgt_off + t;
-    phi_tgt[o] = p;
-    e_part[3 * o] = -gx;
-    e_part[3 * o + 1] = -gy;
-    e_part[3 * o + 2] = -gz;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (c + j >= nc) break;
+        const float4 r0 = rec[2 * (long long)(c + j) * ntgt];
+        const float4 r1 = rec[2 * (long long)(c + j) * ntgt + 1];
+        p[j] = df_add_df(p[j], make_float2(r0.x, r0.y));
+        gx[j] = df_add_df(gx[j], make_float2(r0.z, r0.w));
+        gy[j] = df_add_df(gy[j], make_float2(r1.x, r1.y));
+        gz[j] = df_add_df(gz[j], make_float2(r1.z, r1.w));
+    }
+    auto total = [](const float2 (&v)[4]) {
+        const float2 s = df_add_df(df_add_df(v[0], v[1]), df_add_df(v[2], v[3]));
+        return (double)s.x + (double)s.y;
+    };
+    phi_tgt[o] = total(p);
+    e_part[3 * o] = -total(gx);
+    e_part[3 * o + 1] = -total(gy);
+    e_part[3 * o + 2] = -total(gz);
 }
 
 }  // namespace
 
 // FP32 kernel variants (the autotuner's candidates):
-//   4 = four targets per thread, >= 4 CTAs/SM      5 = four targets, >= 5 CTAs/SM
-//   2 = two targets, >= 6 CTAs/SM
-//  12 = two targets, packed two-source loop, >= 6 CTAs/SM
-//  13 = two targets, packed, >= 5 CTAs/SM         14 = four targets, packed, >= 3 CTAs/SM
+//   4 = four targets per thread, scalar loop, >= 4 CTAs/SM
+//   5 = four targets, scalar, >= 5 CTAs/SM
+//   2 = two targets, scalar, >= 6 CTAs/SM
+//  12 = two targets, packed two-source loop (mode 1), >= 6 CTAs/SM
+//  13 = two targets, packed (mode 1), >= 5 CTAs/SM
+//  14 = four targets, packed (mode 1), >= 3 CTAs/SM
+//  15 = four targets, packed in place, shared accumulators (mode 2), >= 4 CTAs/SM
+//  16 = two targets, packed in place, shared accumulators (mode 2), >= 6 CTAs/SM
 bool pair_variant_valid(int variant)
 {
-    return variant == 4 || variant == 5 || variant == 2 || variant == 12 || variant == 13 || variant == 14;
+    switch (variant) {
+    case 2: case 4: case 5: case 12: case 13: case 14: case 15: case 16: return true;
+    default: return false;
+    }
 }
 
-static int variant_targets(int variant) { return (variant == 2 || variant == 12 || variant == 13) ? 2 : 4; }
-static bool variant_packed(int variant) { return variant >= 12; }
+static int variant_targets(int variant)
+{
+    return (variant == 2 || variant == 12 || variant == 13 || variant == 16) ? 2 : 4;
+}
+static int variant_mode(int variant) { return variant >= 15 ? 2 : (variant >= 12 ? 1 : 0); }
 
 int pair_targets_per_block(int precision, int variant)
 {
@@ -632,9 +762,13 @@ int pair_targets_per_block(int precision, int variant)
 static size_t pair_smem(int precision, int variant)
 {
     if (precision == HSMA_FP64) return 2 * kTile64 * sizeof(double4_32a);
-    // staging: 2 buffers x (hi, lo); packed variants add the interleaved (hi, lo)
+    // staging: 2 buffers x (hi, lo); mode 1 adds the interleaved (hi, lo),
+    // mode 2 the 4T double-float accumulators of every thread
     const size_t tile = (size_t)pair_targets_per_block(precision, variant);
-    return (variant_packed(variant) ? 6 : 4) * tile * sizeof(float4);
+    const int mode = variant_mode(variant);
+    const size_t extra = mode == 1 ? (kCpDouble ? 4 : 2) * tile * sizeof(float4)
+                                   : (mode == 2 ? 4 * (size_t)variant_targets(variant) * kThreads * sizeof(float2) : 0);
+    return 4 * tile * sizeof(float4) + extra;
 }
 
 template <class K>
@@ -651,12 +785,14 @@ int pair_max_ctas_per_sm(int precision, int variant)
     const size_t sm = pair_smem(precision, variant);
     if (precision == HSMA_FP64) return occupancy_of(pair_fp64_kernel, sm);
     switch (variant) {
-    case 2: return occupancy_of(pair_fp32_kernel<2, 6, false>, sm);
-    case 5: return occupancy_of(pair_fp32_kernel<4, 5, false>, sm);
-    case 12: return occupancy_of(pair_fp32_kernel<2, 6, true>, sm);
-    case 13: return occupancy_of(pair_fp32_kernel<2, 5, true>, sm);
-    case 14: return occupancy_of(pair_fp32_kernel<4, 3, true>, sm);
-    default: return occupancy_of(pair_fp32_kernel<4, 4, false>, sm);
+    case 2: return occupancy_of(pair_fp32_kernel<2, 6, 0>, sm);
+    case 5: return occupancy_of(pair_fp32_kernel<4, 5, 0>, sm);
+    case 12: return occupancy_of(pair_fp32_kernel<2, 6, 1>, sm);
+    case 13: return occupancy_of(pair_fp32_kernel<2, 5, 1>, sm);
+    case 14: return occupancy_of(pair_fp32_kernel<4, 3, 1>, sm);
+    case 15: return occupancy_of(pair_fp32_kernel<4, 4, 2>, sm);
+    case 16: return occupancy_of(pair_fp32_kernel<2, 6, 2>, sm);
+    default: return occupancy_of(pair_fp32_kernel<4, 4, 0>, sm);
     }
 }
 
@@ -671,12 +807,14 @@ int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStr
         pair_fp64_kernel<<<grid, kThreads, sm, st>>>(a);
     } else {
         switch (variant) {
-        case 2: pair_fp32_kernel<2, 6, false><<<grid, kThreads, sm, st>>>(a); break;
-        case 5: pair_fp32_kernel<4, 5, false><<<grid, kThreads, sm, st>>>(a); break;
-        case 12: pair_fp32_kernel<2, 6, true><<<grid, kThreads, sm, st>>>(a); break;
-        case 13: pair_fp32_kernel<2, 5, true><<<grid, kThreads, sm, st>>>(a); break;
-        case 14: pair_fp32_kernel<4, 3, true><<<grid, kThreads, sm, st>>>(a); break;
-        default: pair_fp32_kernel<4, 4, false><<<grid, kThreads, sm, st>>>(a); break;
+        case 2: pair_fp32_kernel<2, 6, 0><<<grid, kThreads, sm, st>>>(a); break;
+        case 5: pair_fp32_kernel<4, 5, 0><<<grid, kThreads, sm, st>>>(a); break;
+        case 12: pair_fp32_kernel<2, 6, 1><<<grid, kThreads, sm, st>>>(a); break;
+        case 13: pair_fp32_kernel<2, 5, 1><<<grid, kThreads, sm, st>>>(a); break;
+        case 14: pair_fp32_kernel<4, 3, 1><<<grid, kThreads, sm, st>>>(a); break;
+        case 15: pair_fp32_kernel<4, 4, 2><<<grid, kThreads, sm, st>>>(a); break;
+        case 16: pair_fp32_kernel<2, 6, 2><<<grid, kThreads, sm, st>>>(a); break;
+        default: pair_fp32_kernel<4, 4, 0><<<grid, kThreads, sm, st>>>(a); break;
         }
     }
     HSMA_LAUNCHED();

@@ -70,39 +70,9 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist_kernel(SortArgs a, co
 __global__ void __launch_bounds__(1024) radix_scan_kernel(SortArgs a)
 {
     __shared__ int wsum[32];
-    __shared__ int carry;
+    __shared__ long long carry;
     const SysDesc sd = a.sys[blockIdx.x];
-    const long long total = (long long)kRadix * sd.nblk;
-    int *h = a.hist + sd.hist_off;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long base = 0; base < total; base += blockDim.x) {
-        long long t = base + threadIdx.x;
-        int v = (t < total) ? h[t] : 0;
-        int incl = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int w = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-            int wi = w;
-            for (int o = 1; o < 32; o <<= 1) {
-                int u = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += u;
-            }
-            wsum[lane] = wi - w;
-        }
-        __syncthreads();
-        int excl = carry + wsum[wid] + incl - v;
-        if (t < total) h[t] = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
-        __syncthreads();
-    }
+    block_scan_inplace(a.hist + sd.hist_off, (long long)kRadix * sd.nblk, wsum, &carry);
 }
 
 // Stable scatter of one digit pass: the rank of an element among equal digits

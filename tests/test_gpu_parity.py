@@ -188,7 +188,7 @@ def test_ragged_sizes_fp64(n):
 
 
 # every blocking of the FP32 pair kernel the autotuner may pick
-PAIR_VARIANTS = [4, 5, 2, 12, 13, 14]
+PAIR_VARIANTS = [4, 5, 2, 12, 13, 14, 15, 16]
 
 
 @pytest.mark.parametrize("variant", PAIR_VARIANTS)

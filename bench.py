@@ -64,7 +64,15 @@ def parse():
 
 
 # ------------------------------------------------------- batched workload
-def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_systems: int = 24):
+def fixed_tuning(args):
+    """(pair variant, items per slot) from --tuning, or None (autotune)."""
+    if not args.tuning:
+        return None
+    v, i = (int(t) for t in args.tuning.split(","))
+    return v, i
+
+
+def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_systems: int = 24, fixed=None):
     """256 periodic boxes of log-uniform size in one batched update step
     (persistent launch over all systems, CUDA graph), against the plain
     one-system-per-launch FP64 path."""
@@ -93,8 +101,12 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
         return float(np.median(times)), E
     plan_fp32.set_tuning(4, 24)
     ms_default, _ = timed()
-    plan_fp32.set_tuning(None, None)
-    tuning = plan_fp32.autotune(dx, dq, off)
+    if fixed is None:
+        plan_fp32.set_tuning(None, None)
+        tuning = plan_fp32.autotune(dx, dq, off)
+    else:
+        plan_fp32.set_tuning(*fixed)
+        tuning = {"pair_variant": fixed[0], "items_per_slot": fixed[1], "ms": None, "fixed": True}
     ms, E32 = timed()
     # the plain paths: one system per call (FP64, and FP32 for reference), on
     # a sample of systems
@@ -122,6 +134,23 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
         floor = 0.5 * 2.837297479 * float(np.sum(systems[i][1] ** 2))
         rel.append(abs(E32[i] - U64) / max(abs(U64), floor))
         rel_raw.append(abs(E32[i] - U64) / abs(U64))
+    # the fit of the whole batch (one product over all 256 right-hand sides):
+    # FP64 on the CUDA cores vs split-BF16 on the tensor cores (tcgen05)
+    from paper_1806_04801_gb300 import hsma
+    wb = I.BATCH_PERIODIC
+    fit_ms, e_fit = {}, {}
+    for prec, key in (("fp32", "fp64_fit"), ("fp32_tc", "tensor_core_fit")):
+        with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=prec, profile=True) as pf:
+            pf.set_tuning(tuning["pair_variant"], tuning["items_per_slot"])
+            pf.energy_forces_batched(dx, dq, off)
+            best = None
+            for _ in range(3):
+                e_fit[key], _, _, _ = pf.energy_forces_batched(dx, dq, off)
+                t = pf.last_timings()[3]
+                best = t if best is None else min(best, t)
+            fit_ms[key] = best
+    fit_dev = max(abs(a - b) / max(abs(b), 0.5 * 2.837297479 * float(np.sum(systems[i][1] ** 2)))
+                  for i, (a, b) in enumerate(zip(e_fit["tensor_core_fit"], e_fit["fp64_fit"])))
     # scale the sampled FP64 time to all systems by their share of pair work (~ N^2)
     w_all = float(np.sum(sizes.astype(np.float64) ** 2 + 3000.0 * sizes))
     w_pick = float(np.sum(sizes[pick].astype(np.float64) ** 2 + 3000.0 * sizes[pick]))
@@ -138,7 +167,9 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
             "max_rel_energy_err_vs_fp64": float(max(rel)),
             "max_rel_energy_err_vs_fp64_unfloored": float(max(rel_raw)),
             "energy_err_note": "denominator max(|U|, 1/2 |xi| sum q^2 / L), xi = -2.837297 (self-image scale)",
-            "precision": "fp32 pair sums, fp64 fit, CUDA graph"}
+            "precision": "fp32 pair sums, fp64 fit, CUDA graph",
+            "fit_ms_per_batch": fit_ms,
+            "tensor_core_fit_max_rel_energy_dev": float(fit_dev)}
 
 
 # ------------------------------------------------------ grounded workload
@@ -371,7 +402,7 @@ def main():
                 fl = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
                 with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=args.precision) as pb32, \
                         hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
-                    r = run_batched(pb32, pb64, args.steps, args.warmup, fl)
+                    r = run_batched(pb32, pb64, args.steps, args.warmup, fl, fixed=fixed_tuning(args))
                 line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,
                         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
                         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -405,7 +436,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     if args.tuning:
-        v, i = (int(t) for t in args.tuning.split(","))
+        v, i = fixed_tuning(args)
         plan.set_tuning(v, i)
         tuning = {"pair_variant": v, "items_per_slot": i, "ms": None, "fixed": True}
     else:

@@ -362,7 +362,7 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     w->status = c.take<int>(sh.nsys);
     w->ctrl = c.take<int>(8);
     w->sys = c.take<SysDesc>(sh.nsys);
-    w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys))
+    w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys, p->num_sms))
                                                   : nullptr;
     w->idx64 = c.take<long long>(sh.n_total);
     w->cen = c.take<double4_32a>(sh.n_total);
@@ -501,7 +501,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     // (c) fit
     if (prec == HSMA_FP32_TC_FIT)
         rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
-                           p->mon_inv, w.b, w.A, w.tc_work, st);
+                           p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
     else
         rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A,
                              st);
@@ -852,7 +852,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
                                       st));
         if (prec == HSMA_FP32_TC_FIT)
             rc = launch_fit_tc(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
-                               p->mon_inv, w.b, w.A, w.tc_work, st);
+                               p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
         else
             rc = launch_fit_fp64(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A, st);
         if (rc) return rc;

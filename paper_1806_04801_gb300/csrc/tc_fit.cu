@@ -2,11 +2,16 @@
 // fit, Sec. II.A/II.C), for all systems of a batch at once:
 //   C (ncols x nsys) = M+ (ncols x K) . B (K x nsys),  B(:, s) = b_s.
 // Both operands are split into two BF16 words, x = x_hi + x_lo, and the
-// product is taken as hi.hi + hi.lo + lo.hi with FP32 accumulation
-// (mma.sync m16n8k16, BF16 inputs, FP32 accumulators).  One refinement step
-// follows: r = b - M A in FP64, A += M+ r (again split-BF16 on the tensor
-// cores).  K is padded to a multiple of 16, ncols to 16, nsys to 8 (zeros).
+// product is taken as lo.hi + hi.lo + hi.hi with FP32 accumulation on the
+// 5th-generation tensor cores: tcgen05.mma (kind::f16, BF16 inputs, M = 128,
+// N = up to 256 systems) issued by one thread, operands in shared memory,
+// the accumulator in tensor memory (TMEM), completion through tcgen05.commit
+// on an mbarrier, read back with tcgen05.ld.  One refinement step follows:
+// r = b - M A in FP64, A += M+ r (again split-BF16 on the tensor cores).
+// K is padded to a multiple of 16, ncols to 16, nsys to 8 (zeros).
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -55,57 +60,192 @@ __global__ void rhs_kernel(const SysDesc *sys, int nsys, int bc, int K, int Kp, 
     split_bf16(b, bhi[(long long)s * Kp + i], blo[(long long)s * Kp + i]);
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+// ---------------------------------------------------------------- tcgen05
+// Shared-memory operand layout (no swizzle, K-major): a tile of R rows x 64 K
+// elements is stored as core matrices of 8 rows x 8 elements (8 rows of 16
+// bytes, 128 contiguous bytes); core matrix (row group g, K block kb) sits at
+// byte (g * 8 + kb) * 128.  So the K-direction core-matrix stride (leading
+// byte offset) is 128 B and the row-group stride (stride byte offset) is
+// 1024 B; one MMA (K = 16) starts at K block 2j.
+constexpr int kTcM = 128;          // rows of M+ per CTA (MMA M)
+constexpr int kTcKC = 64;          // K elements staged per round
+constexpr int kTcNMax = 256;       // systems per CTA (MMA N <= 256)
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTcLBO = 128, kTcSBO = 1024;
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr)
 {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);           // start address >> 4, bits [0,14)
+    d |= (uint64_t)(kTcLBO >> 4) << 16;                  // leading (K) byte offset >> 4, bits [16,30)
+    d |= (uint64_t)(kTcSBO >> 4) << 32;                  // stride (row group) byte offset >> 4, bits [32,46)
+    d |= (uint64_t)1 << 46;                              // descriptor version for this architecture
+    return d;                                            // base offset 0, layout: no swizzle
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 in bits [17,23), M >> 4 in bits [24,29).
+__device__ __forceinline__ uint32_t umma_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
-// One warp per 16 x 8 output tile.  A: np x Kp row-major, B: ns8 columns of Kp.
-__global__ void tc_gemm_kernel(int Kp, int np, int ns8, const __nv_bfloat16 *Ahi, const __nv_bfloat16 *Alo,
-                               const __nv_bfloat16 *Bhi, const __nv_bfloat16 *Blo, float *C /* np x ns8 */)
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int tiles_n = ns8 / 8;
-    const int tm = warp / tiles_n, tn = warp % tiles_n;
-    if (tm * 16 >= np) return;
-    const int g = lane >> 2, tg = lane & 3;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const int r0 = tm * 16 + g, r1 = r0 + 8;
-    const int col = tn * 8 + g;
-    for (int k0 = 0; k0 < Kp; k0 += 16) {
-        const int ka = k0 + 2 * tg, kb = ka + 8;
-        uint32_t ah[4], al[4], bh[2], bl[2];
-        ah[0] = pack2(Ahi[(long long)r0 * Kp + ka], Ahi[(long long)r0 * Kp + ka + 1]);
-        ah[1] = pack2(Ahi[(long long)r1 * Kp + ka], Ahi[(long long)r1 * Kp + ka + 1]);
-        ah[2] = pack2(Ahi[(long long)r0 * Kp + kb], Ahi[(long long)r0 * Kp + kb + 1]);
-        ah[3] = pack2(Ahi[(long long)r1 * Kp + kb], Ahi[(long long)r1 * Kp + kb + 1]);
-        al[0] = pack2(Alo[(long long)r0 * Kp + ka], Alo[(long long)r0 * Kp + ka + 1]);
-        al[1] = pack2(Alo[(long long)r1 * Kp + ka], Alo[(long long)r1 * Kp + ka + 1]);
-        al[2] = pack2(Alo[(long long)r0 * Kp + kb], Alo[(long long)r0 * Kp + kb + 1]);
-        al[3] = pack2(Alo[(long long)r1 * Kp + kb], Alo[(long long)r1 * Kp + kb + 1]);
-        bh[0] = pack2(Bhi[(long long)col * Kp + ka], Bhi[(long long)col * Kp + ka + 1]);
-        bh[1] = pack2(Bhi[(long long)col * Kp + kb], Bhi[(long long)col * Kp + kb + 1]);
-        bl[0] = pack2(Blo[(long long)col * Kp + ka], Blo[(long long)col * Kp + ka + 1]);
-        bl[1] = pack2(Blo[(long long)col * Kp + kb], Blo[(long long)col * Kp + kb + 1]);
-        mma_bf16(acc, al, bh);
-        mma_bf16(acc, ah, bl);
-        mma_bf16(acc, ah, bh);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Stage rows [row0, row0 + R) x K [k0, k0 + kTcKC) of a row-major BF16
+// matrix (rows of length Kp, rows >= nrows and K >= Kp read as zero) into
+// the core-matrix layout above.  Every 16-byte piece is one row of a core
+// matrix.
+__device__ __forceinline__ void tc_stage(const __nv_bfloat16 *src, int nrows, int Kp, int row0, int k0, int R,
+                                         unsigned char *dst)
+{
+    const int pieces = R * (kTcKC / 8);
+    for (int q = threadIdx.x; q < pieces; q += kTcThreads) {
+        const int r = q / (kTcKC / 8), kb = q % (kTcKC / 8);
+        const int row = row0 + r, k = k0 + kb * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (row < nrows && k < Kp) v = *reinterpret_cast<const uint4 *>(src + (long long)row * Kp + k);
+        *reinterpret_cast<uint4 *>(dst + ((r >> 3) * 8 + kb) * 128 + (r & 7) * 16) = v;
     }
-    const int oc = tn * 8 + 2 * tg;
-    C[(long long)r0 * ns8 + oc] = acc[0];
-    C[(long long)r0 * ns8 + oc + 1] = acc[1];
-    C[(long long)r1 * ns8 + oc] = acc[2];
-    C[(long long)r1 * ns8 + oc + 1] = acc[3];
+}
+
+// One CTA: rows [m0, m0 + 128) x systems [n0, n0 + N) of the product over
+// the K rounds [z rps, (z + 1) rps) (split K, z = blockIdx.z).  A: np x Kp,
+// B: ns8 rows (one per system) of Kp; P: [split][np x ns8] FP32 partials.
+__global__ void __launch_bounds__(kTcThreads) tc_gemm_kernel(int Kp, int np, int ns8, const __nv_bfloat16 *Ahi,
+                                                             const __nv_bfloat16 *Alo, const __nv_bfloat16 *Bhi,
+                                                             const __nv_bfloat16 *Blo, int rps, float *P,
+                                                             int *status, int nsys)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int m0 = blockIdx.x * kTcM, n0 = blockIdx.y * kTcNMax;
+    const int N = min(kTcNMax, (ns8 - n0 + 15) / 16 * 16);          // MMA N: multiple of 16
+    const uint32_t tcols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    unsigned char *a_hi = tc_smem, *a_lo = a_hi + kTcM * kTcKC * 2;
+    unsigned char *b_hi = a_lo + kTcM * kTcKC * 2, *b_lo = b_hi + kTcNMax * kTcKC * 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = umma_idesc_bf16(kTcM, N);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int kbeg = blockIdx.z * rps * kTcKC, kend = min(Kp, kbeg + rps * kTcKC);
+    float *C = P + (long long)blockIdx.z * np * ns8;
+    for (int k0 = kbeg; k0 < kend; k0 += kTcKC) {
+        tc_stage(Ahi, np, Kp, m0, k0, kTcM, a_hi);
+        tc_stage(Alo, np, Kp, m0, k0, kTcM, a_lo);
+        tc_stage(Bhi, ns8, Kp, n0, k0, N, b_hi);
+        tc_stage(Blo, ns8, Kp, n0, k0, N, b_lo);
+        fence_proxy_async_smem();  // generic writes -> tensor-core (async proxy) reads
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int steps = min(kTcKC, Kp - k0) / 16;
+            for (int j = 0; j < steps; ++j) {
+                const uint32_t off = (uint32_t)(2 * j) * 128u;
+                const uint64_t ah = umma_smem_desc(smem_u32(a_hi) + off), al = umma_smem_desc(smem_u32(a_lo) + off);
+                const uint64_t bh = umma_smem_desc(smem_u32(b_hi) + off), bl = umma_smem_desc(smem_u32(b_lo) + off);
+                umma_bf16(tmem, al, bh, idesc, (k0 > kbeg || j > 0) ? 1 : 0);
+                umma_bf16(tmem, ah, bl, idesc, 1);
+                umma_bf16(tmem, ah, bh, idesc, 1);
+            }
+            umma_commit(&bar);  // arrives once the MMAs above have read shared memory and written TMEM
+        }
+        // the staged operands are rewritten next round: wait for the MMAs
+        if (!mbar_wait_bounded(&bar, phase)) ok = false;
+        phase ^= 1u;
+        __syncthreads();
+        if (!ok) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // warp w reads TMEM lanes [32 w, 32 w + 32) = rows m0 + 32 w + lane
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < np) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < ns8) C[(long long)row * ns8 + col] = __uint_as_float(v[j]);
+                }
+            }
+        }
+    } else {
+        // give MMAs still in flight a bounded chance to finish before TMEM is freed
+        mbar_wait_bounded(&bar, phase ^ 1u, 200000000LL);
+        if (threadIdx.x == 0)
+            for (int s2 = n0; s2 < min(nsys, n0 + N); ++s2) atomicOr(&status[s2], ST_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+constexpr size_t kTcSmem = (size_t)2 * kTcM * kTcKC * 2 + (size_t)2 * kTcNMax * kTcKC * 2;
+
+// C = sum of the split-K partials, in split order (deterministic).
+__global__ void tc_reduce_kernel(long long n, int split, const float *P, float *C)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float c = 0.f;
+    for (int z = 0; z < split; ++z) c += P[(long long)z * n + i];
+    C[i] = c;
+}
+
+// Split of the K rounds over CTAs: enough CTAs to cover the SMs once, every
+// CTA at least one round.
+struct TcSplit {
+    int mt, nt, rounds, rps, split;
+};
+TcSplit tc_split(int K, int ncols, int nsys, int sms)
+{
+    TcSplit t;
+    const int Kp = pad16(K), np = pad16(ncols), ns8 = pad8(nsys);
+    t.mt = (np + kTcM - 1) / kTcM;
+    t.nt = (ns8 + kTcNMax - 1) / kTcNMax;
+    t.rounds = (Kp + kTcKC - 1) / kTcKC;
+    int want = std::max(1, std::min(t.rounds, (sms + t.mt * t.nt - 1) / (t.mt * t.nt)));
+    t.rps = (t.rounds + want - 1) / want;
+    t.split = (t.rounds + t.rps - 1) / t.rps;
+    return t;
 }
 
 // A1 = C; residual r = b - M A1 (FP64), split into BF16 columns.
@@ -140,14 +280,18 @@ __global__ void combine_kernel(int nsys, int ncols, int ns8, int Nb, int drop, c
 
 size_t tc_operand_bytes(int K, int ncols) { return (size_t)pad16(ncols) * pad16(K) * sizeof(__nv_bfloat16); }
 
-size_t tc_work_bytes(int K, int ncols, int nsys)
+size_t tc_work_bytes(int K, int ncols, int nsys, int sms)
 {
     size_t Kp = pad16(K), np = pad16(ncols), ns8 = pad8(nsys);
-    return 2 * ns8 * Kp * sizeof(__nv_bfloat16) * 2 + 2 * np * ns8 * sizeof(float) + (size_t)ncols * nsys * 8 + 4096;
+    const TcSplit t = tc_split(K, ncols, nsys, sms);
+    return 2 * ns8 * Kp * sizeof(__nv_bfloat16) * 2 + 2 * np * ns8 * sizeof(float) + (size_t)ncols * nsys * 8 +
+           (size_t)t.split * np * ns8 * sizeof(float) + 16 * 256;  // + rounding of each piece
 }
 
 int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *Mp_lo, cudaStream_t st)
 {
+    // dynamic shared memory of the GEMM, set once here (outside any graph capture)
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     int Kp = pad16(K), np = pad16(ncols);
     long long tot = (long long)np * Kp;
     split_matrix_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(K, ncols, Kp, np, Mp, (__nv_bfloat16 *)Mp_hi,
@@ -159,8 +303,9 @@ int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *M
 
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
                   const void *Mp_lo, const double *Mrow, const double *phi_tgt, const int *mon_inv, double *b_out,
-                  double *A, float *work, cudaStream_t st)
+                  double *A, float *work, int *status, int sms, cudaStream_t st)
 {
+    const TcSplit ts = tc_split(K, ncols, nsys, sms);
     const int Kp = pad16(K), np = pad16(ncols), ns8 = pad8(nsys);
     char *w = (char *)work;
     auto take = [&](size_t bytes) {
@@ -175,16 +320,23 @@ int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb
     float *C1 = (float *)take((size_t)np * ns8 * 4);
     float *C2 = (float *)take((size_t)np * ns8 * 4);
     double *A1 = (double *)take((size_t)ncols * nsys * 8);
+    float *Pz = (float *)take((size_t)ts.split * np * ns8 * 4);
     const __nv_bfloat16 *ahi = (const __nv_bfloat16 *)Mp_hi, *alo = (const __nv_bfloat16 *)Mp_lo;
     dim3 g1((Kp + 255) / 256, ns8);
     rhs_kernel<<<g1, 256, 0, st>>>(sys, nsys, bc, K, Kp, phi_tgt, mon_inv, b_out, bhi, blo);
     HSMA_LAUNCHED();
-    const int warps = (np / 16) * (ns8 / 8);
-    tc_gemm_kernel<<<(warps + 3) / 4, 128, 0, st>>>(Kp, np, ns8, ahi, alo, bhi, blo, C1);
+    const dim3 gg(ts.mt, ts.nt, ts.split);
+    const long long nc = (long long)np * ns8;
+    const unsigned gr = (unsigned)((nc + 255) / 256);
+    tc_gemm_kernel<<<gg, kTcThreads, kTcSmem, st>>>(Kp, np, ns8, ahi, alo, bhi, blo, ts.rps, Pz, status, nsys);
+    HSMA_LAUNCHED();
+    tc_reduce_kernel<<<gr, 256, 0, st>>>(nc, ts.split, Pz, C1);
     HSMA_LAUNCHED();
     residual_kernel<<<g1, 256, 0, st>>>(nsys, K, Kp, ncols, ns8, Mrow, b_out, C1, A1, rhi, rlo);
     HSMA_LAUNCHED();
-    tc_gemm_kernel<<<(warps + 3) / 4, 128, 0, st>>>(Kp, np, ns8, ahi, alo, rhi, rlo, C2);
+    tc_gemm_kernel<<<gg, kTcThreads, kTcSmem, st>>>(Kp, np, ns8, ahi, alo, rhi, rlo, ts.rps, Pz, status, nsys);
+    HSMA_LAUNCHED();
+    tc_reduce_kernel<<<gr, 256, 0, st>>>(nc, ts.split, Pz, C2);
     HSMA_LAUNCHED();
     dim3 g3((ncols + 127) / 128, nsys);
     combine_kernel<<<g3, 128, 0, st>>>(nsys, ncols, ns8, Nb, bc == HSMA_BC_PERIODIC ? 1 : 0, A1, C2, A);

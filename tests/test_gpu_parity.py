@@ -8,7 +8,7 @@ launch configuration the benchmark times.
 import numpy as np
 import pytest
 
-from gpu_common import TOL, assert_within, errors, rms, to_dev
+from gpu_common import TOL, assert_within, errors, rel_energy_err, rms, to_dev
 from paper_1806_04801_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -185,6 +185,44 @@ def test_ragged_sizes_fp64(n):
     with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
         U, F, _, _ = plan.energy_forces(dx, dq)
         assert_within(errors(F.cpu().numpy(), ref["forces"], U, ref["energy"]), "fp32", f"n={n}")
+
+
+def test_tensor_core_fit_matches_fp64_fit(small_periodic, grounded_small):
+    """The fit on the tensor cores (split-BF16 products, FP32 accumulation in
+    tensor memory, one FP64-residual refinement) against the FP64 fit of the
+    same monitoring potentials: the FP32 and tensor-core forms share the pair
+    kernel, so b is identical and A differs only by the fit's arithmetic.
+    Each operand is held to ~1e-5 relative by its two BF16 words; the
+    refinement removes that error from the fitted part of b but not from the
+    least-squares residual e = b - M A*, so the coefficients agree to about
+    1e-5 |e| / |b| (~2e-7 here).  A product term left out (lo.hi or hi.lo)
+    would leave >= 4e-5, a wrong operand layout O(1)."""
+    cases = [(small_periodic[0], small_periodic[1], I.SMALL_PERIODIC),
+             (grounded_small[1], grounded_small[2], grounded_small[0])]
+    for xyz, q, w in cases:
+        res = {}
+        for prec in ("fp32", "fp32_tc"):
+            with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+                plan.energy_forces(*to_dev(xyz, q))
+                nb = (w.p + 1) ** 2
+                res[prec] = (plan.last_get(1, w.Kmon), plan.last_get(0, nb))
+        b32, A32 = res["fp32"]
+        btc, Atc = res["fp32_tc"]
+        assert np.array_equal(b32, btc)
+        assert rms(Atc - A32) <= 2e-6 * rms(A32), (w.name, rms(Atc - A32) / rms(A32))
+    # a batch: the tensor-core product spans several systems (MMA N)
+    systems = [I.uniform_pm1(int(n), (1.0, 1.0, 1.0), seed_offset=700 + i) for i, n in enumerate([300, 1200, 50, 2000, 800])]
+    xyz = np.concatenate([a for a, _ in systems])
+    q = np.concatenate([b for _, b in systems])
+    off = np.concatenate([[0], np.cumsum([len(b) for _, b in systems])])
+    w = I.SMALL_PERIODIC
+    E = {}
+    for prec in ("fp32", "fp32_tc"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            E[prec], _, _, st = plan.energy_forces_batched(*to_dev(xyz, q), off)
+            assert np.all(st == 0)
+    for i in range(len(systems)):
+        assert rel_energy_err(E["fp32_tc"][i], E["fp32"][i], systems[i][1]) <= 5e-7, i
 
 
 # every blocking of the FP32 pair kernel the autotuner may pick

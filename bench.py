@@ -445,6 +445,8 @@ def main():
         plan.energy_forces(dx, dq)
     torch.cuda.synchronize()
 
+    # measured FP32 throughput of this device, beside the count-based peak
+    fp32_meas = hsma.fp32_peak() if args.precision != "fp64" else None
     clocks = ClockSampler()
     if rank == 0:
         clocks.start(local)
@@ -561,7 +563,11 @@ def main():
                      "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
                                    f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",
-                     "kernel_ms": pair_avg_ms, "share_of_step": pair_avg_ms / ms_per_step},
+                     "kernel_ms": pair_avg_ms, "share_of_step": pair_avg_ms / ms_per_step,
+                     "measured_fp32": ({"scalar_fma": fp32_meas[0] / 1e12, "packed_fma": fp32_meas[1] / 1e12,
+                                        "frac_of_scalar_fma": achieved / fp32_meas[0],
+                                        "how": "hsma_fp32_peak: register-only FMA chains, 16 CTAs/SM"}
+                                       if fp32_meas else None)},
         "roofline_surface": {"bound": "alu", "kernel": "surface_pairs_fp32_kernel",
                              "achieved": OPS_SURFACE * pairs_surf / (phases[5] / 1000.0) / 1e12,
                              "peak": peak_ops / 1e12, "unit": "T FP32 lane-instructions/s",

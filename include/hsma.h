@@ -374,6 +374,15 @@ int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const dou
  * part, without the Condon-Shortley phase.  Errors: HSMA_E_ARG, HSMA_E_CUDA. */
 int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, void *stream);
 
+/* ------------------------------------------------------ device peaks */
+/* Measured FP32 throughput of the current device (no counterpart in the
+ * paper): independent register-only FMA chains, scalar (fmaf) and packed
+ * (fma.rn.f32x2, two lanes per instruction), 16 CTAs of 128 threads per SM,
+ * best of three timed launches on a private stream.  Outputs: lane FMAs per
+ * second (one FMA of one lane = 1).  Synchronous; takes ~10 ms.  Errors:
+ * HSMA_E_ARG (NULL output), HSMA_E_CUDA. */
+int hsma_fp32_peak(double *scalar_lane_ops_per_s, double *packed_lane_ops_per_s);
+
 /* --------------------------------------------------------- inspection */
 const char *hsma_strerror(int code);
 const char *hsma_version(void);

@@ -16,7 +16,9 @@
 // accurate to a few FP32 ulps of the distance itself, even for the closest
 // pairs; 1/r comes from the SFU (rsqrt.approx); the potential is summed in
 // FP32 over 32 sources and the field over a whole tile, then folded into
-// double-float (hi, lo) accumulators with an error-free TwoSum.
+// double-float (hi, lo) accumulators with an error-free TwoSum.  The packed
+// variants run the same arithmetic on two sources per f32x2 instruction
+// (fma/add/mul.rn.f32x2), which halves the issue slots of the FP32 work.
 //
 // FP64 form: the same loop in double, rsqrt() from the CUDA math library.
 #include "common.cuh"
@@ -26,9 +28,9 @@ namespace hsma {
 namespace {
 
 constexpr int kThreads = 128;
-// FP32 form: T targets per thread (T = 4 or 2); a block of 128 T targets is
-// exactly one in-set tile of 128 T sources, so a particle block's box is its
-// tile's box.
+// FP32 form: T targets per thread (T = 4 or 2, by variant); a block of 128 T
+// targets is exactly one in-set tile of 128 T sources, so a particle block's
+// box is its tile's box.
 constexpr int kT64 = 2;
 constexpr int kTB64 = kThreads * kT64;
 constexpr int kTile64 = 256;

@@ -76,6 +76,7 @@ SIGNATURES = {
     "hsma_strerror": (ctypes.c_char_p, [_I]),
     "hsma_version": (ctypes.c_char_p, []),
     "hsma_kernel_launches": (_I64, []),
+    "hsma_fp32_peak": (_I, [_VP, _VP]),
     "hsma_last_timings": (_I, [_VP, _VP, _I]),
     "hsma_last_get": (_I64, [_VP, _I, _VP, _I64]),
     "hsma_plan_set_tuning": (_I, [_VP, ctypes.POINTER(hsma_tuning)]),
@@ -141,6 +142,16 @@ def _stream_handle(stream):
 
 def kernel_launches() -> int:
     return int(_lib().hsma_kernel_launches())
+
+
+def fp32_peak() -> tuple:
+    """hsma_fp32_peak: measured (scalar, packed) FP32 lane FMAs per second of
+    the current device."""
+    sc, pk = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = _lib().hsma_fp32_peak(ctypes.byref(sc), ctypes.byref(pk))
+    if rc != 0:
+        raise HsmaError(rc, "hsma_fp32_peak")
+    return sc.value, pk.value
 
 
 def version() -> str:

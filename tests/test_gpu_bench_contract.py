@@ -35,6 +35,23 @@ def test_bench_json_line():
     assert r["gpu_launches"] >= 3 * 10
     assert r["accuracy"]["rel_energy_err"] <= 1e-6
     assert "workload" in r["config"]
+    m = rf["measured_fp32"]
+    assert m and 0 < m["packed_fma"] and 0 < m["scalar_fma"] <= 1.05 * rf["peak"]
+    assert abs(m["frac_of_scalar_fma"] - rf["achieved"] / m["scalar_fma"]) < 1e-9
+
+
+def test_fp32_peak_probe():
+    """The measured FP32 FMA throughput lies between half and all of the
+    count-based lane peak (SMs x 128 lanes x 2070 MHz): no probe can beat the
+    lane count, and independent chains at 16 CTAs/SM cannot fall far short."""
+    import torch
+    from paper_1806_04801_gb300 import build, hsma
+    build.build()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2070e6
+    sc, pk = hsma.fp32_peak()
+    assert 0.5 * nominal < sc <= 1.02 * nominal, (sc, nominal)
+    assert 0.5 * nominal < pk <= 1.02 * nominal, (pk, nominal)
 
 
 def test_reference_arm_json_line():

@@ -531,7 +531,7 @@ def main():
         extras["serving"] = run_serving(args.requests)
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is an N = 1 figure
         r = cpu_oracle_rate(xyz, q, w)
         cpu = {"value": r["systems_per_s"], "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
                "sample": (f"full monitoring-point sums and fit, near-field particle sums on "

@@ -40,7 +40,7 @@ RECIPE_MAX_SM_MHZ = 2070.0
 # periodic N=100000 workload, from the ncu capture summarised in
 # profiles/pair_fp32_kernel_periodic_N100000_dram.md (current kernel build),
 # keyed by (N, pair variant, items per slot) of the captured launch.
-PAIR_FP32_TRAFFIC_BYTES = {(100_000, 14, 48): 358.17e6}
+PAIR_FP32_TRAFFIC_BYTES = {(100_000, 14, 48): 356.89e6}
 OPS_SURFACE = 45                 # FP32 lane instructions per particle-direction pair of the surface kernel
 
 
@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp32_tc"])
+    ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp64", "fp32_tc"],
+                    help="fp32_tc (default): FP32 pair sums with double-float accumulation, split-BF16 "
+                         "tensor-core fit + one refinement; fp32: the same with an FP64 fit; fp64: parity form")
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -167,7 +169,7 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
             "max_rel_energy_err_vs_fp64": float(max(rel)),
             "max_rel_energy_err_vs_fp64_unfloored": float(max(rel_raw)),
             "energy_err_note": "denominator max(|U|, 1/2 |xi| sum q^2 / L), xi = -2.837297 (self-image scale)",
-            "precision": "fp32 pair sums, fp64 fit, CUDA graph",
+            "precision": f"{plan_fp32.precision}: fp32 pair sums ({'split-BF16 tensor-core' if plan_fp32.precision == 'fp32_tc' else 'fp64'} fit), CUDA graph",
             "fit_ms_per_batch": fit_ms,
             "tensor_core_fit_max_rel_energy_dev": float(fit_dev)}
 
@@ -220,7 +222,7 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
     def replay(rate, count, seed):
         t_arr, sizes = I.poisson_trace(count, rate_hz=rate, seed_offset=4 + seed)
         reqs = [I.uniform_pm1(int(n), w.box, seed_offset=5000 + seed * 1000 + i) for i, n in enumerate(sizes)]
-        with hsma.Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=lanes,
+        with hsma.Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32_tc", lanes=lanes,
                          max_batch=max_batch) as srv:
             # warm the lanes (plans, workspaces)
             for _ in range(lanes):
@@ -525,7 +527,7 @@ def main():
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
         wb = I.BATCH_PERIODIC
-        with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp32") as pb32, \
+        with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=args.precision) as pb32, \
                 hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
             extras = {"batched": run_batched(pb32, pb64, max(3, min(args.steps, 5)), 2, flush)}
         extras["serving"] = run_serving(args.requests)
@@ -559,7 +561,7 @@ def main():
                      "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "T FP32 lane-instructions/s", "frac": achieved / peak_ops,
                      "traffic": (PAIR_FP32_TRAFFIC_BYTES.get((n, tuning["pair_variant"], tuning["items_per_slot"]))
-                                 if args.precision == "fp32" else None),
+                                 if args.precision != "fp64" else None),
                      "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
                      "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
                                    f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",

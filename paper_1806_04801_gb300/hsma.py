@@ -184,6 +184,8 @@ class Plan:
                "hsma_plan")
         self._h = h
         self.box = tuple(float(b) for b in box)
+        codes = {v: k for k, v in PRECISIONS.items()}
+        self.precision = codes.get(o.precision, str(o.precision))  # "fp64", "fp32" or "fp32_tc"
 
     # ------------------------------------------------------------- info
     @property

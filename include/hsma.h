@@ -72,8 +72,10 @@ typedef enum { HSMA_BC_PERIODIC = 0, HSMA_BC_GROUNDED = 1 } hsma_bc;
  *                     into double-float accumulators; fit, mapping and energy
  *                     in FP64.
  *  HSMA_FP32_TC_FIT   as HSMA_FP32_ACC64, but the fit A = M+ b runs on the
- *                     tensor cores as a split-BF16 product with FP32
- *                     accumulation plus one refinement step. */
+ *                     tensor cores (tcgen05) as a split-BF16 product with
+ *                     FP32 accumulation in tensor memory, plus one
+ *                     refinement step (residual b - M A in FP64, correction
+ *                     again on the tensor cores). */
 typedef enum { HSMA_FP64 = 0, HSMA_FP32_ACC64 = 1, HSMA_FP32_TC_FIT = 2 } hsma_precision;
 
 typedef struct {

@@ -74,8 +74,9 @@ typedef enum { HSMA_BC_PERIODIC = 0, HSMA_BC_GROUNDED = 1 } hsma_bc;
  *  HSMA_FP32_TC_FIT   as HSMA_FP32_ACC64, but the fit A = M+ b runs on the
  *                     tensor cores (tcgen05) as a split-BF16 product with
  *                     FP32 accumulation in tensor memory, plus one
- *                     refinement step (residual b - M A in FP64, correction
- *                     again on the tensor cores). */
+ *                     refinement step (residual b - M A in double-float
+ *                     arithmetic on the FP32 pipe, correction again on the
+ *                     tensor cores). */
 typedef enum { HSMA_FP64 = 0, HSMA_FP32_ACC64 = 1, HSMA_FP32_TC_FIT = 2 } hsma_precision;
 
 typedef struct {

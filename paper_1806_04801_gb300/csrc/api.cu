@@ -118,6 +118,7 @@ struct hsma_plan_s {
     double4_32a *dirs = nullptr;
     int4 *shifts = nullptr;
     void *tc_hi = nullptr, *tc_lo = nullptr;
+    void *tc_mdf = nullptr;  // M (K x n_cols) as FP32 word pairs, for the refinement residual
     // workspace
     void *ws_mem = nullptr;
     size_t ws_cap = 0;
@@ -500,7 +501,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
 
     // (c) fit
     if (prec == HSMA_FP32_TC_FIT)
-        rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
+        rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->tc_mdf, w.phi_tgt,
                            p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
     else
         rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A,
@@ -851,7 +852,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
         HSMA_CUDA_TRY(cudaMemcpyAsync(w.phi_tgt + n, mon.data(), sizeof(double) * p->nmon, cudaMemcpyHostToDevice,
                                       st));
         if (prec == HSMA_FP32_TC_FIT)
-            rc = launch_fit_tc(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->Mrow, w.phi_tgt,
+            rc = launch_fit_tc(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->tc_mdf, w.phi_tgt,
                                p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
         else
             rc = launch_fit_fp64(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A, st);
@@ -1064,6 +1065,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         pl->shifts = c.take<int4>(sh.size());
         pl->tc_hi = c.take<char>(tc_operand_bytes(K, ncols));
         pl->tc_lo = c.take<char>(tc_operand_bytes(K, ncols));
+        pl->tc_mdf = c.take<char>(tc_residual_matrix_bytes(K, ncols));
         if (pass == 0) {
             if (cudaMalloc(&pl->plan_mem, align_up(c.off, 256)) != cudaSuccess) {
                 cudaGetLastError();
@@ -1128,7 +1130,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         if ((rc = launch_quadrature(F2, F1, R, pl->dirs, st))) break;
         // basis at Rs u_j == basis of the unit vector u_j with unit radius
         if ((rc = launch_basis(p, 1.0, ndir, (const double *)pl->dirs, 4, pl->norm, pl->Bq, Nb, st))) break;
-        if ((rc = prepare_tc_operands(K, ncols, pl->Mp, pl->tc_hi, pl->tc_lo, st))) break;
+        if ((rc = prepare_tc_operands(K, ncols, pl->Mp, pl->Mrow, pl->tc_hi, pl->tc_lo, pl->tc_mdf, st))) break;
         if ((rc = sort_monitor_targets(pl, st))) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) {
             rc = HSMA_E_CUDA;

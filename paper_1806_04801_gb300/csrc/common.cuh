@@ -355,10 +355,12 @@ void plan_trim_workspace(hsma_plan_t plan, size_t max_keep);
 
 // tc_fit.cu
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
-                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, const int *mon_inv, double *b_out,
+                  const void *Mp_lo, const void *Mdf, const double *phi_tgt, const int *mon_inv, double *b_out,
                   double *A, float *work, int *status, int sms, cudaStream_t st);
-int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *Mp_lo, cudaStream_t st);
+int prepare_tc_operands(int K, int ncols, const double *Mp, const double *Mrow, void *Mp_hi, void *Mp_lo, void *Mdf,
+                        cudaStream_t st);
 size_t tc_operand_bytes(int K, int ncols);
+size_t tc_residual_matrix_bytes(int K, int ncols);
 size_t tc_work_bytes(int K, int ncols, int nsys, int sms);
 
 }  // namespace hsma

@@ -7,7 +7,8 @@
 // N = up to 256 systems) issued by one thread, operands in shared memory,
 // the accumulator in tensor memory (TMEM), completion through tcgen05.commit
 // on an mbarrier, read back with tcgen05.ld.  One refinement step follows:
-// r = b - M A in FP64, A += M+ r (again split-BF16 on the tensor cores).
+// r = b - M A in double-float arithmetic on the FP32 pipe, A += M+ r (again
+// split-BF16 on the tensor cores).
 // K is padded to a multiple of 16, ncols to 16, nsys to 8 (zeros).
 #include <cuda_bf16.h>
 
@@ -248,8 +249,20 @@ TcSplit tc_split(int K, int ncols, int nsys, int sms)
     return t;
 }
 
-// A1 = C; residual r = b - M A1 (FP64), split into BF16 columns.
-__global__ void residual_kernel(int nsys, int K, int Kp, int ncols, int ns8, const double *Mrow, const double *b,
+// A1 = C; residual r = b - M A1 in double-float arithmetic on the FP32 pipe
+// (M held as FP32 word pairs, each product split exactly with an FMA, sums
+// by TwoSum; ~1e-14 relative, like FP64 at a fraction of its cost on this
+// part), split into BF16 columns.
+__device__ __forceinline__ float2 df_mul_f(float2 m, float c)
+{
+    const float p = m.x * c;
+    float e = fmaf(m.x, c, -p);  // exact error of the high product
+    e = fmaf(m.y, c, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+
+__global__ void residual_kernel(int nsys, int K, int Kp, int ncols, int ns8, const float2 *Mdf, const double *b,
                                 const float *C, double *A1, __nv_bfloat16 *rhi, __nv_bfloat16 *rlo)
 {
     int s = blockIdx.y;
@@ -257,13 +270,27 @@ __global__ void residual_kernel(int nsys, int K, int Kp, int ncols, int ns8, con
     if (i >= Kp) return;
     double r = 0.0;
     if (s < nsys && i < K) {
-        double acc = 0.0;
-        const double *row = Mrow + (long long)i * ncols;
-        for (int c = 0; c < ncols; ++c) acc += row[c] * (double)C[(long long)c * ns8 + s];
-        r = b[(long long)s * K + i] - acc;
+        float2 acc = make_float2(0.f, 0.f);
+        const float2 *row = Mdf + (long long)i * ncols;
+        for (int c = 0; c < ncols; ++c) acc = df_add_df(acc, df_mul_f(row[c], C[(long long)c * ns8 + s]));
+        const double bi = b[(long long)s * K + i];
+        const float bh = (float)bi;
+        const float2 bdf = make_float2(bh, (float)(bi - (double)bh));
+        const float2 rd = df_add_df(bdf, make_float2(-acc.x, -acc.y));
+        r = (double)rd.x + (double)rd.y;
         if (i < ncols) A1[(long long)s * ncols + i] = (double)C[(long long)i * ns8 + s];
     }
     split_bf16(r, rhi[(long long)s * Kp + i], rlo[(long long)s * Kp + i]);
+}
+
+// M (K x n_cols, FP64) as FP32 word pairs.
+__global__ void split_rows_kernel(long long n, const double *M, float2 *Mdf)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double v = M[t];
+    const float h = (float)v;
+    Mdf[t] = make_float2(h, (float)(v - (double)h));
 }
 
 __global__ void combine_kernel(int nsys, int ncols, int ns8, int Nb, int drop, const double *A1, const float *C2,
@@ -280,6 +307,8 @@ __global__ void combine_kernel(int nsys, int ncols, int ns8, int Nb, int drop, c
 
 size_t tc_operand_bytes(int K, int ncols) { return (size_t)pad16(ncols) * pad16(K) * sizeof(__nv_bfloat16); }
 
+size_t tc_residual_matrix_bytes(int K, int ncols) { return (size_t)K * ncols * sizeof(float2); }
+
 size_t tc_work_bytes(int K, int ncols, int nsys, int sms)
 {
     size_t Kp = pad16(K), np = pad16(ncols), ns8 = pad8(nsys);
@@ -288,8 +317,12 @@ size_t tc_work_bytes(int K, int ncols, int nsys, int sms)
            (size_t)t.split * np * ns8 * sizeof(float) + 16 * 256;  // + rounding of each piece
 }
 
-int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *Mp_lo, cudaStream_t st)
+int prepare_tc_operands(int K, int ncols, const double *Mp, const double *Mrow, void *Mp_hi, void *Mp_lo, void *Mdf,
+                        cudaStream_t st)
 {
+    const long long nm = (long long)K * ncols;
+    split_rows_kernel<<<(unsigned)((nm + 255) / 256), 256, 0, st>>>(nm, Mrow, (float2 *)Mdf);
+    HSMA_LAUNCHED();
     // dynamic shared memory of the GEMM, set once here (outside any graph capture)
     HSMA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     int Kp = pad16(K), np = pad16(ncols);
@@ -302,7 +335,7 @@ int prepare_tc_operands(int K, int ncols, const double *Mp, void *Mp_hi, void *M
 }
 
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
-                  const void *Mp_lo, const double *Mrow, const double *phi_tgt, const int *mon_inv, double *b_out,
+                  const void *Mp_lo, const void *Mdf, const double *phi_tgt, const int *mon_inv, double *b_out,
                   double *A, float *work, int *status, int sms, cudaStream_t st)
 {
     const TcSplit ts = tc_split(K, ncols, nsys, sms);
@@ -332,7 +365,7 @@ int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb
     HSMA_LAUNCHED();
     tc_reduce_kernel<<<gr, 256, 0, st>>>(nc, ts.split, Pz, C1);
     HSMA_LAUNCHED();
-    residual_kernel<<<g1, 256, 0, st>>>(nsys, K, Kp, ncols, ns8, Mrow, b_out, C1, A1, rhi, rlo);
+    residual_kernel<<<g1, 256, 0, st>>>(nsys, K, Kp, ncols, ns8, (const float2 *)Mdf, b_out, C1, A1, rhi, rlo);
     HSMA_LAUNCHED();
     tc_gemm_kernel<<<gg, kTcThreads, kTcSmem, st>>>(Kp, np, ns8, ahi, alo, rhi, rlo, ts.rps, Pz, status, nsys);
     HSMA_LAUNCHED();

@@ -108,12 +108,17 @@ def _mixed_traffic(server, systems, first, results):
         results.append((first + j, t))
 
 
-def test_serving_alone_and_in_mix_agree():
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc"])
+def test_serving_alone_and_in_mix_agree(prec):
+    """A request served alone and inside concurrent traffic (continuous
+    batching over two lanes) agrees within the reduced-form tolerance; so
+    does every mixed request with a direct call.  With the tensor-core fit the
+    product spans whatever systems share the batch."""
     w = I.SERVING_PERIODIC
     target_x, target_q = I.uniform_pm1(12000, w.box, seed_offset=70)
     others = [I.uniform_pm1(int(n), w.box, seed_offset=71 + i) for i, n in
               enumerate([1000, 30000, 5000, 2000, 60000, 800, 15000, 4000, 9000, 3000])]
-    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=2, max_batch=8) as srv:
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec, lanes=2, max_batch=8) as srv:
         t = srv.submit(target_x, target_q)
         code, E_alone, F_alone, info = srv.result(t, n=len(target_q))
         assert code == 0 and info["batch_size"] == 1
@@ -129,7 +134,7 @@ def test_serving_alone_and_in_mix_agree():
         assert rel_energy_err(E_mix, E_alone, target_q) <= TOL["fp32"]["energy"]
         assert rms(F_mix - F_alone) <= TOL["fp32"]["force_rms"] * rms(F_alone)
         # every mixed request agrees with a direct single-system call
-        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
             for j, tk in tickets:
                 sx, sq = others[j]
                 code, E, F, inf = srv.result(tk, n=len(sq))

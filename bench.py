@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
-    ap.add_argument("--workload", default="periodic", choices=["periodic", "batched", "serving", "grounded"])
+    ap.add_argument("--workload", default="periodic", choices=["periodic", "batched", "serving", "grounded", "basis"])
+    ap.add_argument("--basis-points", type=int, default=4_000_000, help="points of the basis workload")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the Poisson trace")
     ap.add_argument("--tuning", default=None,
                     help="V,I: fix the pair kernel variant and items per slot instead of autotuning "
@@ -66,6 +67,56 @@ def parse():
 
 
 # ------------------------------------------------------- batched workload
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (generated file), else
+    the recorded fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_basis(steps: int, warmup: int, n: int = 4_000_000, p: int = 12, Rs: float = 1.5):
+    """The harmonic basis of Eq. "harmonic" (orthonormal real solid harmonics,
+    N_b = (p + 1)^2 per point, FP64) at n points spread over the auxiliary
+    sphere's ball: the per-point evaluation behind the plan's matrices and
+    the direct series evaluation, timed through hsma_basis."""
+    import torch
+    from paper_1806_04801_gb300 import hsma
+    g = torch.Generator(device="cuda").manual_seed(1806_04801 + 5)
+    pts = (torch.rand(n, 3, dtype=torch.float64, device="cuda", generator=g) - 0.5) * (2.0 * Rs / math.sqrt(3.0))
+    for _ in range(warmup):
+        out = hsma.basis(pts, p, Rs)
+        del out
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = hsma.basis(pts, p, Rs)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        del out
+    ms = float(np.median(times))
+    nb = (p + 1) ** 2
+    written = n * nb * 8.0
+    hbm, how = measured_hbm_gbs()
+    # FP64 operations of the recurrence per point: per (n, m) with n >= m + 2
+    # five (two products, a fused difference, the reciprocal), per stored
+    # value two (norm x Pi x C_m or S_m), plus the (x + i y)^m update
+    pairs = sum(max(0, p - m - 1) for m in range(p + 1))
+    fp64_ops = 5 * pairs + 2 * nb + 4 * p + 8
+    return {"workload": f"basis-N{n}-p{p} (points uniform in a cube inside the Rs = {Rs} ball)",
+            "points": n, "p": p, "N_b": nb, "ms": ms, "points_per_s": n / (ms / 1000.0),
+            "roofline": {"bound": "fp64", "achieved_gbs": written / (ms / 1000.0) / 1e9, "peak_gbs": hbm,
+                         "hbm_frac": written / (ms / 1000.0) / 1e9 / hbm, "peak_basis": f"HBM copy bandwidth, {how}",
+                         "fp64_ops_per_point": fp64_ops,
+                         "achieved_fp64_tops": n * fp64_ops / (ms / 1000.0) / 1e12,
+                         "note": "one thread per point computes the FP64 recurrence; FP64 issue bounds it on this part"}}
+
+
 def fixed_tuning(args):
     """(pair variant, items per slot) from --tuning, or None (autotune)."""
     if not args.tuning:
@@ -409,6 +460,13 @@ def main():
                         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
                         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                         "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
+            elif args.workload == "basis":
+                r = run_basis(args.steps, args.warmup, n=args.basis_points)
+                line = {"metric": "harmonic basis evaluations/s (Eq. harmonic) and HBM GB/s written",
+                        "value": r["points_per_s"], "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+                        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
+                        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                        "config": {"workload": r["workload"]}, "roofline": r["roofline"], "detail": r}
             elif args.workload == "grounded":
                 r = run_grounded(args.steps, args.warmup)
                 line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,

@@ -85,7 +85,7 @@ __global__ void surface_charges_kernel(int ndir, int Nb, const double *Bq, const
 // kSurfSplit-th direction of each staged tile (more warps per SM for the
 // same work), and their partial sums are added in group order at the end.
 constexpr int kSurfThreads = 256;
-constexpr int kSurfSplit = 4;
+constexpr int kSurfSplit = 8;
 constexpr int kSurfGroup = kSurfThreads / kSurfSplit;
 constexpr int kSurfT = 2;
 constexpr int kSurfTB = kSurfGroup * kSurfT;

@@ -9,7 +9,7 @@ Update step (Sec. II.C): images inside the auxiliary sphere, the right-hand
 side of the least-squares problem, the coefficients A_nm, the surface images
 Q_j (Sec. II.B) and finally energies and forces.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * periodic monitoring points: the Fibonacci latitude grid on the circumsphere
     of the box; the fitting residual is Phi(x_i) - Phi(x~_i) (Sec. II.A);
   * the n = 0 column of the periodic fitting matrix is identically zero

@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
-    ap.add_argument("--workload", default="periodic", choices=["periodic", "batched", "serving", "grounded", "basis"])
+    ap.add_argument("--workload", default="periodic",
+                    choices=["periodic", "batched", "serving", "grounded", "basis", "paper"])
     ap.add_argument("--basis-points", type=int, default=4_000_000, help="points of the basis workload")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the Poisson trace")
     ap.add_argument("--tuning", default=None,
@@ -115,6 +116,42 @@ def run_basis(steps: int, warmup: int, n: int = 4_000_000, p: int = 12, Rs: floa
                          "fp64_ops_per_point": fp64_ops,
                          "achieved_fp64_tops": n * fp64_ops / (ms / 1000.0) / 1e12,
                          "note": "one thread per point computes the FP64 recurrence; FP64 issue bounds it on this part"}}
+
+
+def run_paper_config(steps: int, warmup: int, precision: str, n_side: int = 47):
+    """The configuration of the paper's timing study (Sec. III): unit charges
+    of random sign on a uniform lattice (47^3 = 103823 sites, about the
+    paper's N = 100k), periodic, alpha = 1.3, P = 25, N_o = 5928 (F2 = 987);
+    the paper reports under 1 s per HSMA step there on two Tesla P100 or two
+    K80 GPUs (precision not stated)."""
+    import torch
+    from paper_1806_04801_gb300 import hsma
+    from paper_1806_04801_gb300 import inputs as I
+    L = (1.0, 1.0, 1.0)
+    alpha, P = 1.3, 25
+    Rs = alpha * 0.5 * math.sqrt(3.0)
+    xyz, q = I.lattice_random_sign(n_side, 1.0, seed_offset=500 + n_side)
+    dx, dq = torch.as_tensor(xyz).cuda(), torch.as_tensor(q).cuda()
+    with hsma.Plan(L, I.PERIODIC, P, Rs, 5928, 2 * P * P, precision=precision, fib_F2=987, profile=True) as plan:
+        plan.autotune(dx, dq)
+        for _ in range(warmup):
+            plan.energy_forces(dx, dq)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            U, _, _, ns = plan.energy_forces(dx, dq)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        info = plan.info()
+    ms = float(np.median(times))
+    return {"workload": f"paper timing configuration: lattice {n_side}^3 random +-1, periodic, alpha 1.3 "
+                        f"(Rs = {Rs:.4f} L), P = 25, N_o = {info['n_images']}, Kmon = {2 * P * P}",
+            "N": int(len(q)), "n_inset": int(ns), "ms_per_step": ms, "systems_per_s": 1000.0 / ms,
+            "precision": precision, "energy": float(U),
+            "paper": "under 1 s per step on 2x Tesla P100 or 2x Tesla K80 (Sec. III; precision not stated)"}
 
 
 def fixed_tuning(args):
@@ -467,6 +504,12 @@ def main():
                         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True,
                         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                         "config": {"workload": r["workload"]}, "roofline": r["roofline"], "detail": r}
+            elif args.workload == "paper":
+                r = run_paper_config(args.steps, args.warmup, args.precision)
+                line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,
+                        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                        "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
             elif args.workload == "grounded":
                 r = run_grounded(args.steps, args.warmup)
                 line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,
@@ -589,6 +632,7 @@ def main():
                 hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
             extras = {"batched": run_batched(pb32, pb64, max(3, min(args.steps, 5)), 2, flush)}
         extras["serving"] = run_serving(args.requests)
+        extras["paper_config"] = run_paper_config(max(3, min(args.steps, 5)), 2, args.precision)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is an N = 1 figure

@@ -510,13 +510,109 @@ __global__ void series_field_kernel(const SysDesc *sys, int nsys, int P, double 
 
 }  // namespace
 
+// FP32 form of series_field_kernel for the reduced precisions: the same
+// recurrences in FP32 (positions from the split words, coefficients
+// pre-multiplied by the normalisation and the reciprocals 1/(n - m) staged in
+// shared memory), the sums over n folded into double-float accumulators after
+// every m.  FP64 issue is slow on this part; this evaluates the fitted
+// series at O(N N_b) FP32 cost.
+constexpr int kSeriesMaxP = 40;
+__global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, double inv_rs, const double *norm,
+                                         const double *A, const float4 *src_hi, const float4 *src_lo,
+                                         double *phi_out, double *e_out)
+{
+    extern __shared__ float ssm[];  // [Nb] coefficients A_k norm_k, then [P + 1] reciprocals
+    const int s = blockIdx.y;
+    const SysDesc sd = sys[s];
+    const int Nb = (P + 1) * (P + 1);
+    float *an = ssm, *rinv = ssm + Nb;
+    const double *a = A + (long long)s * Nb;
+    for (int k = threadIdx.x; k < Nb; k += blockDim.x) an[k] = (float)(a[k] * norm[k]);
+    for (int k = threadIdx.x; k <= P; k += blockDim.x) rinv[k] = k > 0 ? 1.0f / (float)k : 0.f;
+    __syncthreads();
+    const long long i = sd.sp_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sd.sp_lo + sd.sp_n) return;
+    const float4 h = src_hi[sd.src_off + i], l = src_lo[sd.src_off + i];
+    const float ir = (float)inv_rs;
+    const float x = (h.x + l.x) * ir, y = (h.y + l.y) * ir, z = (h.z + l.z) * ir;
+    const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+    float2 phi = make_float2(0.f, 0.f), gx = phi, gy = phi, gz = phi;
+    float cm = 1.f, sm = 0.f, cp = 0.f, sp = 0.f;  // (x+iy)^m and (x+iy)^(m-1)
+    float pmm = 1.f, two_m_1 = -1.f;
+    for (int m = 0; m <= P; ++m) {
+        if (m > 0) {
+            cp = cm;
+            sp = sm;
+            const float c2 = cm * x - sm * y;
+            sm = sm * x + cm * y;
+            cm = c2;
+            pmm *= two_m_1;
+        }
+        const float fm = (float)m;
+        float p1 = 0.f, p2 = 0.f, z1 = 0.f, z2 = 0.f, q1 = 0.f, q2 = 0.f;
+        float a_n = two_m_1 + 4.f, b_n = 2.f * fm + 1.f;  // 2n - 1 and n + m - 1 at n = m + 2
+        float fp = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        for (int n = m; n <= P; ++n) {
+            float pn, dz, dq;
+            if (n == m) {
+                pn = pmm;
+                dz = 0.f;
+                dq = 0.f;
+            } else if (n == m + 1) {
+                pn = (two_m_1 + 2.f) * z * pmm;
+                dz = (two_m_1 + 2.f) * pmm;
+                dq = 0.f;
+            } else {
+                const float inv = rinv[n - m];
+                pn = (a_n * z * p1 - b_n * r2 * p2) * inv;
+                dz = (a_n * (p1 + z * z1) - b_n * r2 * z2) * inv;
+                dq = (a_n * z * q1 - b_n * (p2 + r2 * q2)) * inv;
+                a_n += 2.f;
+                b_n += 1.f;
+            }
+            p2 = p1; p1 = pn;
+            z2 = z1; z1 = dz;
+            q2 = q1; q1 = dq;
+            const float rx = 2.f * dq * x, ry = 2.f * dq * y, rz = dz + 2.f * dq * z;
+            const float ac = an[n * n + n + m];
+            fp += ac * pn * cm;
+            fx += ac * (pn * fm * cp + cm * rx);
+            fy += ac * (-pn * fm * sp + cm * ry);
+            fz += ac * (cm * rz);
+            if (m > 0) {
+                const float as = an[n * n + n - m];
+                fp += as * pn * sm;
+                fx += as * (pn * fm * sp + sm * rx);
+                fy += as * (pn * fm * cp + sm * ry);
+                fz += as * (sm * rz);
+            }
+        }
+        phi = df_add(phi, fp);
+        gx = df_add(gx, fx);
+        gy = df_add(gy, fy);
+        gz = df_add(gz, fz);
+        two_m_1 += 2.f;
+    }
+    const long long o = sd.part_off + i;
+    phi_out[o] = (double)phi.x + (double)phi.y;
+    e_out[3 * o] = -((double)gx.x + (double)gx.y) * inv_rs;
+    e_out[3 * o + 1] = -((double)gy.x + (double)gy.y) * inv_rs;
+    e_out[3 * o + 2] = -((double)gz.x + (double)gz.y) * inv_rs;
+}
+
 int launch_series_field(const SysDesc *sys, int nsys, long long max_n, int P, double Rs, const double *norm,
                         const double *A, const float4 *src_hi, const float4 *src_lo, const double4_32a *src64,
                         double *phi_out, double *e_out, cudaStream_t st)
 {
     dim3 grid((unsigned)((max_n + 127) / 128), nsys);
-    series_field_kernel<<<grid, 128, 0, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, src64, phi_out,
-                                              e_out);
+    if (!src64 && src_hi && P <= kSeriesMaxP) {
+        const size_t smem = sizeof(float) * ((size_t)(P + 1) * (P + 1) + (size_t)(P + 1));
+        series_field_fp32_kernel<<<grid, 128, smem, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, phi_out,
+                                                          e_out);
+    } else {
+        series_field_kernel<<<grid, 128, 0, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, src64, phi_out,
+                                                  e_out);
+    }
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

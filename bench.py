@@ -208,7 +208,9 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         return float(np.median(times)), E
-    plan_fp32.set_tuning(4, 24)
+    plan_fp32.set_tuning(4, 24)  # the scalar loop, for reference
+    ms_scalar, _ = timed()
+    plan_fp32.set_tuning(None, None)  # the library's untuned default
     ms_default, _ = timed()
     if fixed is None:
         plan_fp32.set_tuning(None, None)
@@ -267,7 +269,8 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
     t32_all = t32 * w_all / w_pick
     return {"workload": "batched-256-periodic-p10 (N log-uniform in [500, 50000], +-1)",
             "systems": len(systems), "particles": int(off[-1]), "ms_per_batch": ms,
-            "autotuned": tuning, "ms_per_batch_default_tiles": ms_default,
+            "autotuned": tuning, "ms_per_batch_default_tuning": ms_default,
+            "ms_per_batch_scalar_variant_4_24": ms_scalar,
             "systems_per_s": len(systems) / (ms / 1000.0),
             "fp64_one_system_per_launch_systems_per_s": len(systems) / (t64_all / 1000.0),
             "fp32_one_system_per_launch_systems_per_s": len(systems) / (t32_all / 1000.0),

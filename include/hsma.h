@@ -238,7 +238,8 @@ int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *ph
  *   items_per_slot  work items per resident CTA slot (source chunks are sized
  *                   so that a call has about this many items per slot)
  *   ms              time measured by hsma_autotune (0 otherwise)
- * Defaults: 4 and 24. */
+ * Defaults (no tuning entry for the call's work size): variant 14 for one
+ * system, 12 for a batch, 48 items per slot (FP64: 24 items). */
 typedef struct {
     int pair_variant;
     int items_per_slot;

@@ -241,7 +241,10 @@ hsma_tuning choose_tuning(const hsma_plan_s *p, int nsys, const long long *n)
             best = &e.second;
         }
     }
-    return best ? *best : hsma_tuning{4, 24, 0.0};
+    if (best) return *best;
+    // untuned: the packed variants measured fastest on this part, four targets
+    // per thread for one system, two for a batch
+    return p->precision == HSMA_FP64 ? hsma_tuning{4, 24, 0.0} : hsma_tuning{nsys > 1 ? 12 : 14, 48, 0.0};
 }
 
 void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precision, const hsma_tuning &tu,

@@ -111,19 +111,26 @@ __device__ __forceinline__ int find_sys_surf(const SysDesc *sys, int nsys, int i
 //   its field:    (p/dr)((d + h u)/A^3 - (d - h u)/B^3)
 //                 = p [ -2 a (A^2 + A B + B^2) / ((A + B) A^3 B^3) d
 //                       + (u/2)(1/A^3 + 1/B^3) ]
-__global__ void __launch_bounds__(kSurfThreads, 4) surface_pairs_fp32_kernel(
+//
+// Each thread takes two directions of its group per step with packed FP32
+// instructions (fma/add/mul.rn.f32x2 on the pair); the group's directions
+// of a staged tile are stored pair-interleaved: sx = (u_x, u_x', u_y, u_y'),
+// sy = (u_z, u_z', Q, Q'), sz = (-2 p, -2 p', p/2, p'/2).  Slots beyond the
+// tile hold a direction with Q = p = 0, which contributes exactly zero.
+constexpr int kSurfPairs = kSurfTile / kSurfSplit / 2;  // direction pairs per group per tile
+
+__global__ void __launch_bounds__(kSurfThreads, 2) surface_pairs_fp32_kernel(
     const SysDesc *sys, int nsys, const float4 *src_hi, const float4 *src_lo, int ndir, const double4_32a *dirs,
     const double2 *img, float Rs, float h, double *phi_out, double *e_out)
 {
-    __shared__ float4 su[kSurfTile];   // (u_x, u_y, u_z, Q_sigma)
-    __shared__ float sp[kSurfTile];    // p
+    __shared__ float4 sx[kSurfSplit][kSurfPairs], sy[kSurfSplit][kSurfPairs], sz[kSurfSplit][kSurfPairs];
     __shared__ float2 red[kSurfSplit - 1][kSurfT][4][kSurfGroup];  // partial sums of groups 1..
     const int s = find_sys_surf(sys, nsys, blockIdx.x);
     const SysDesc sd = sys[s];
     const int blk = blockIdx.x - sd.surf_off;
     const int gl = threadIdx.x % kSurfGroup;  // particle lane
     const int grp = threadIdx.x / kSurfGroup;  // direction group (uniform per warp)
-    float rx[kSurfT], ry[kSurfT], rz[kSurfT];
+    float2 RX[kSurfT], RY[kSurfT], RZ[kSurfT];  // particle position, both lanes
     long long idx[kSurfT];
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
@@ -135,10 +142,13 @@ __global__ void __launch_bounds__(kSurfThreads, 4) surface_pairs_fp32_kernel(
             a = src_hi[sd.src_off + i];
             b = src_lo[sd.src_off + i];
         }
-        rx[t] = a.x + b.x;
-        ry[t] = a.y + b.y;
-        rz[t] = a.z + b.z;
+        const float rx = a.x + b.x, ry = a.y + b.y, rz = a.z + b.z;
+        RX[t] = make_float2(rx, rx);
+        RY[t] = make_float2(ry, ry);
+        RZ[t] = make_float2(rz, rz);
     }
+    const float2 NRS = make_float2(-Rs, -Rs), HH = make_float2(h * h, h * h);
+    const float2 H2 = make_float2(2.f * h, 2.f * h), NH2 = make_float2(-2.f * h, -2.f * h);
     float2 phi[kSurfT], e[kSurfT][3];
 #pragma unroll
     for (int t = 0; t < kSurfT; ++t) {
@@ -146,56 +156,85 @@ __global__ void __launch_bounds__(kSurfThreads, 4) surface_pairs_fp32_kernel(
         e[t][0] = e[t][1] = e[t][2] = make_float2(0.f, 0.f);
     }
     const double2 *im = img + (long long)s * ndir;
+    float *fx = reinterpret_cast<float *>(&sx[0][0]), *fy = reinterpret_cast<float *>(&sy[0][0]);
+    float *fz = reinterpret_cast<float *>(&sz[0][0]);
     for (int d0 = 0; d0 < ndir; d0 += kSurfTile) {
-        int cnt = min(kSurfTile, ndir - d0);
+        const int cnt = min(kSurfTile, ndir - d0);
         __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += kSurfThreads) {
-            double4_32a u = dirs[d0 + j];
-            double2 c = im[d0 + j];
-            bool live = u.w > 0.0;
-            su[j] = make_float4((float)u.x, (float)u.y, (float)u.z, live ? (float)c.x : 0.f);
-            sp[j] = live ? (float)c.y : 0.f;
+        for (int j = threadIdx.x; j < kSurfTile; j += kSurfThreads) {
+            float ux = 1.f, uy = 0.f, uz = 0.f, Q = 0.f, pw = 0.f;
+            if (j < cnt) {
+                const double4_32a u = dirs[d0 + j];
+                const double2 c = im[d0 + j];
+                const bool live = u.w > 0.0;
+                ux = (float)u.x;
+                uy = (float)u.y;
+                uz = (float)u.z;
+                Q = live ? (float)c.x : 0.f;
+                pw = live ? (float)c.y : 0.f;
+            }
+            const int g = j % kSurfSplit, k = j / kSurfSplit, kp = k >> 1, ln = k & 1;
+            const int base = (g * kSurfPairs + kp) * 4;
+            fx[base + ln] = ux;
+            fx[base + 2 + ln] = uy;
+            fy[base + ln] = uz;
+            fy[base + 2 + ln] = Q;
+            fz[base + ln] = -2.f * pw;
+            fz[base + 2 + ln] = 0.5f * pw;
         }
         __syncthreads();
-        float pa[kSurfT], ea[kSurfT][3];
+        const int cg = cnt > grp ? (cnt - grp + kSurfSplit - 1) / kSurfSplit : 0;  // this group's directions
+        const int npairs = (cg + 1) >> 1;
+        float2 pa[kSurfT], ea[kSurfT][3];
 #pragma unroll
-        for (int t = 0; t < kSurfT; ++t) pa[t] = ea[t][0] = ea[t][1] = ea[t][2] = 0.f;
-        for (int j = grp; j < cnt; j += kSurfSplit) {
-            const float4 u = su[j];
-            const float p = sp[j];
+        for (int t = 0; t < kSurfT; ++t) {
+            pa[t] = make_float2(0.f, 0.f);
+            ea[t][0] = ea[t][1] = ea[t][2] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 2
+        for (int kp = 0; kp < npairs; ++kp) {
+            const float4 X = sx[grp][kp], Y = sy[grp][kp], Z = sz[grp][kp];
+            const float2 ux = make_float2(X.x, X.y), uy = make_float2(X.z, X.w);
+            const float2 uz = make_float2(Y.x, Y.y), Q = make_float2(Y.z, Y.w);
+            const float2 np2 = make_float2(Z.x, Z.y), hp = make_float2(Z.z, Z.w);
 #pragma unroll
             for (int t = 0; t < kSurfT; ++t) {
-                float dx = fmaf(-Rs, u.x, rx[t]);
-                float dy = fmaf(-Rs, u.y, ry[t]);
-                float dz = fmaf(-Rs, u.z, rz[t]);
-                float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                float ad = fmaf(u.x, dx, fmaf(u.y, dy, u.z * dz));
-                float base = fmaf(h, h, dd);
-                float A2 = fmaf(2.f * h, ad, base);
-                float B2 = fmaf(-2.f * h, ad, base);
-                float ri = rsqrt_sfu(dd);
-                float Ai = rsqrt_sfu(A2);
-                float Bi = rsqrt_sfu(B2);
-                float Aa = A2 * Ai, Bb = B2 * Bi;
-                float inv_sum = __fdividef(1.f, Aa + Bb);
-                float qs = u.w * ri;
-                float dip = -2.f * p * ad * Ai * Bi * inv_sum;
-                pa[t] += qs + dip;
-                float ri3 = ri * ri * ri;
-                float Ai3 = Ai * Ai * Ai, Bi3 = Bi * Bi * Bi;
-                float cd = u.w * ri3 - 2.f * p * ad * (A2 + Aa * Bb + B2) * inv_sum * Ai3 * Bi3;
-                float cu = 0.5f * p * (Ai3 + Bi3);
-                ea[t][0] += fmaf(cd, dx, cu * u.x);
-                ea[t][1] += fmaf(cd, dy, cu * u.y);
-                ea[t][2] += fmaf(cd, dz, cu * u.z);
+                const float2 dx = __ffma2_rn(NRS, ux, RX[t]);
+                const float2 dy = __ffma2_rn(NRS, uy, RY[t]);
+                const float2 dz = __ffma2_rn(NRS, uz, RZ[t]);
+                const float2 dd = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                const float2 ad = __ffma2_rn(ux, dx, __ffma2_rn(uy, dy, __fmul2_rn(uz, dz)));
+                const float2 base = __fadd2_rn(dd, HH);
+                const float2 A2 = __ffma2_rn(H2, ad, base);
+                const float2 B2 = __ffma2_rn(NH2, ad, base);
+                const float2 ri = make_float2(rsqrt_sfu(dd.x), rsqrt_sfu(dd.y));
+                const float2 Ai = make_float2(rsqrt_sfu(A2.x), rsqrt_sfu(A2.y));
+                const float2 Bi = make_float2(rsqrt_sfu(B2.x), rsqrt_sfu(B2.y));
+                const float2 Aa = __fmul2_rn(A2, Ai), Bb = __fmul2_rn(B2, Bi);
+                const float2 sab = __fadd2_rn(Aa, Bb);
+                const float2 inv = make_float2(__fdividef(1.f, sab.x), __fdividef(1.f, sab.y));
+                const float2 qs = __fmul2_rn(Q, ri);
+                const float2 m1 = __fmul2_rn(np2, ad);                                   // -2 p a
+                const float2 dip = __fmul2_rn(__fmul2_rn(m1, __fmul2_rn(Ai, Bi)), inv);  // dipole potential
+                pa[t] = __fadd2_rn(pa[t], __fadd2_rn(qs, dip));
+                const float2 ri3 = __fmul2_rn(__fmul2_rn(ri, ri), ri);
+                const float2 Ai3 = __fmul2_rn(__fmul2_rn(Ai, Ai), Ai);
+                const float2 Bi3 = __fmul2_rn(__fmul2_rn(Bi, Bi), Bi);
+                const float2 S = __fadd2_rn(__ffma2_rn(Aa, Bb, A2), B2);  // A^2 + A B + B^2
+                const float2 cd = __fadd2_rn(
+                    __fmul2_rn(Q, ri3), __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(m1, S), inv), Ai3), Bi3));
+                const float2 cu = __fmul2_rn(hp, __fadd2_rn(Ai3, Bi3));
+                ea[t][0] = __fadd2_rn(ea[t][0], __ffma2_rn(cd, dx, __fmul2_rn(cu, ux)));
+                ea[t][1] = __fadd2_rn(ea[t][1], __ffma2_rn(cd, dy, __fmul2_rn(cu, uy)));
+                ea[t][2] = __fadd2_rn(ea[t][2], __ffma2_rn(cd, dz, __fmul2_rn(cu, uz)));
             }
         }
 #pragma unroll
         for (int t = 0; t < kSurfT; ++t) {
-            phi[t] = df_add(phi[t], pa[t]);
-            e[t][0] = df_add(e[t][0], ea[t][0]);
-            e[t][1] = df_add(e[t][1], ea[t][1]);
-            e[t][2] = df_add(e[t][2], ea[t][2]);
+            phi[t] = df_add(phi[t], pa[t].x + pa[t].y);
+            e[t][0] = df_add(e[t][0], ea[t][0].x + ea[t][0].y);
+            e[t][1] = df_add(e[t][1], ea[t][1].x + ea[t][1].y);
+            e[t][2] = df_add(e[t][2], ea[t][2].x + ea[t][2].y);
         }
     }
     // add the groups' partial sums in group order

@@ -233,13 +233,14 @@ int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *ph
  *                   packed, at 3 CTAs per SM; 15, 16 = four / two targets
  *                   per thread, packed, tile interleaved in place and the
  *                   double-float sums in shared memory, at 4 / 6 CTAs per
- *                   SM; ignored in FP64.  Any other value is HSMA_E_ARG in
- *                   hsma_plan_set_tuning
+ *                   SM; 17 = three targets per thread (blocks and tiles of
+ *                   384), packed, at 4 CTAs per SM; ignored in FP64.  Any
+ *                   other value is HSMA_E_ARG in hsma_plan_set_tuning
  *   items_per_slot  work items per resident CTA slot (source chunks are sized
  *                   so that a call has about this many items per slot)
  *   ms              time measured by hsma_autotune (0 otherwise)
  * Defaults (no tuning entry for the call's work size): variant 14 for one
- * system, 12 for a batch, 48 items per slot (FP64: 24 items). */
+ * system, 17 for a batch, 48 items per slot (FP64: 24 items). */
 typedef struct {
     int pair_variant;
     int items_per_slot;
@@ -256,7 +257,7 @@ int hsma_plan_set_tuning(hsma_plan_t plan, const hsma_tuning *t);
 int hsma_plan_get_tuning(hsma_plan_t plan, int nsys, const int64_t *offsets, hsma_tuning *out);
 
 /* Autotuner: runs the update step on this batch for each candidate
- * (pair_variant 4, 5, 2, 12, 13, 14, 15, 16 x items_per_slot 8, 16, 24, 48; FP64:
+ * (pair_variant 4, 5, 2, 12, 13, 14, 15, 16, 17 x items_per_slot 8, 16, 24, 48; FP64:
  * items only), keeps the fastest as
  * the plan's entry for this work size, returns it in *best, and appends it as
  * one JSON line to cache_path (if not NULL).  Device inputs are recommended

@@ -99,7 +99,8 @@ struct hsma_plan_s {
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
     int num_sms, ctas[3];
-    int ctas_var[16] = {};  // FP32 pair kernel: resident CTAs per SM, by variant code
+    static constexpr int kVariantCodes = 32;
+    int ctas_var[kVariantCodes] = {};  // FP32 pair kernel: resident CTAs per SM, by variant code
     // tuning of the pair kernel: a fixed choice, or entries per work bucket
     bool tune_fixed = false;
     hsma_tuning tune_value{4, 24, 0.0};
@@ -112,6 +113,7 @@ struct hsma_plan_s {
     // monitoring targets in spatial (Morton) order for the pair kernel
     double4_32a *mon64_s = nullptr;
     float4 *mon_hi_s = nullptr, *mon_lo_s = nullptr, *mon_boxes = nullptr, *mon_boxes2 = nullptr;
+    float4 *mon_boxes3 = nullptr;  // monitoring-target block boxes for blocks of 512 / 256 / 384
     int *mon_perm_d = nullptr, *mon_inv = nullptr;
     std::vector<int> mon_perm;
     double *Mrow = nullptr, *Mp = nullptr, *Bq = nullptr, *norm = nullptr;
@@ -211,7 +213,8 @@ int ensure_pinned(hsma_plan_s *p, size_t bytes)
 int tuned_ctas(const hsma_plan_s *p, int precision, int variant)
 {
     if (precision == HSMA_FP64) return p->ctas[0];
-    return (variant > 0 && variant < 16 && p->ctas_var[variant] > 0) ? p->ctas_var[variant] : p->ctas[1];
+    return (variant > 0 && variant < hsma_plan_s::kVariantCodes && p->ctas_var[variant] > 0) ? p->ctas_var[variant]
+                                                                                             : p->ctas[1];
 }
 
 // Pair work of a batch (targets x estimated in-set sources), and its bucket
@@ -243,8 +246,8 @@ hsma_tuning choose_tuning(const hsma_plan_s *p, int nsys, const long long *n)
     }
     if (best) return *best;
     // untuned: the packed variants measured fastest on this part, four targets
-    // per thread for one system, two for a batch
-    return p->precision == HSMA_FP64 ? hsma_tuning{4, 24, 0.0} : hsma_tuning{nsys > 1 ? 12 : 14, 48, 0.0};
+    // per thread for one system, three for a batch
+    return p->precision == HSMA_FP64 ? hsma_tuning{4, 24, 0.0} : hsma_tuning{nsys > 1 ? 17 : 14, 48, 0.0};
 }
 
 void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precision, const hsma_tuning &tu,
@@ -488,7 +491,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.ext_field = 0;
     pa.ext_skip_zero = 0;
     pa.boxes = w.boxes;
-    pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
+    pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : (TB == 384 ? p->mon_boxes3 : p->mon_boxes)) : nullptr;
     pa.stall_test = p->stall_test;
     pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
     pa.partials = w.partials;
@@ -713,6 +716,8 @@ int sort_monitor_targets(hsma_plan_s *p, cudaStream_t st)
     if (rc) return rc;
     rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64, 2), p->mon_boxes2, st);
     if (rc) return rc;
+    rc = launch_array_boxes(n, p->mon_hi_s, pair_targets_per_block(HSMA_FP32_ACC64, 17), p->mon_boxes3, st);
+    if (rc) return rc;
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));  // host vectors above go out of scope
     return HSMA_OK;
 }
@@ -833,7 +838,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
         pa.ext_field = 0;
         pa.ext_skip_zero = 0;
         pa.boxes = w.boxes;
-        pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : p->mon_boxes) : nullptr;
+        pa.ext_boxes = w.boxes ? (TB == 256 ? p->mon_boxes2 : (TB == 384 ? p->mon_boxes3 : p->mon_boxes)) : nullptr;
         pa.far2 = (float)(p->far_rel * p->Rs * p->far_rel * p->Rs);
         pa.partials = w.partials;
         pa.next_item = w.ctrl;
@@ -1028,7 +1033,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     pl->num_sms = prop.multiProcessorCount;
     pl->ctas[0] = pair_max_ctas_per_sm(HSMA_FP64);
     pl->ctas[1] = pl->ctas[2] = pair_max_ctas_per_sm(HSMA_FP32_ACC64, 4);
-    for (int v = 1; v < 16; ++v)
+    for (int v = 1; v < hsma_plan_s::kVariantCodes; ++v)
         if (pair_variant_valid(v)) pl->ctas_var[v] = pair_max_ctas_per_sm(HSMA_FP32_ACC64, v);
     snprintf(pl->device_name, sizeof(pl->device_name), "%s", prop.name);
 
@@ -1058,6 +1063,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         pl->mon_lo_s = c.take<float4>(nmon);
         pl->mon_boxes = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
         pl->mon_boxes2 = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
+        pl->mon_boxes3 = c.take<float4>(2 * ((nmon + 255) / 256 + 1));
         pl->mon_perm_d = c.take<int>(nmon);
         pl->mon_inv = c.take<int>(nmon);
         pl->Mrow = c.take<double>((size_t)K * ncols);
@@ -1363,9 +1369,9 @@ int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_p
     const hsma_tuning value0 = pl->tune_value;
     std::vector<double> energies(nsys);
     std::vector<hsma_tuning> cands;
-    const int variants[8] = {4, 5, 2, 12, 13, 14, 15, 16};
+    const int variants[9] = {4, 5, 2, 12, 13, 14, 15, 16, 17};
     const int items[4] = {8, 16, 24, 48};
-    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 8); ++v)
+    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 9); ++v)
         for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
     hsma_tuning win{4, 24, 1e300};
     int rc = HSMA_OK;

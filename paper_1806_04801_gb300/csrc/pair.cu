@@ -742,19 +742,21 @@ __global__ void partial_reduce_kernel(const SysDesc *sys, int n_ext, const float
 //  14 = four targets, packed (mode 1), >= 3 CTAs/SM
 //  15 = four targets, packed in place, shared accumulators (mode 2), >= 4 CTAs/SM
 //  16 = two targets, packed in place, shared accumulators (mode 2), >= 6 CTAs/SM
+//  17 = three targets (blocks and tiles of 384), packed (mode 1), >= 4 CTAs/SM
 bool pair_variant_valid(int variant)
 {
     switch (variant) {
-    case 2: case 4: case 5: case 12: case 13: case 14: case 15: case 16: return true;
+    case 2: case 4: case 5: case 12: case 13: case 14: case 15: case 16: case 17: return true;
     default: return false;
     }
 }
 
 static int variant_targets(int variant)
 {
+    if (variant == 17) return 3;
     return (variant == 2 || variant == 12 || variant == 13 || variant == 16) ? 2 : 4;
 }
-static int variant_mode(int variant) { return variant >= 15 ? 2 : (variant >= 12 ? 1 : 0); }
+static int variant_mode(int variant) { return variant == 17 ? 1 : (variant >= 15 ? 2 : (variant >= 12 ? 1 : 0)); }
 
 int pair_targets_per_block(int precision, int variant)
 {
@@ -794,6 +796,7 @@ int pair_max_ctas_per_sm(int precision, int variant)
     case 14: return occupancy_of(pair_fp32_kernel<4, 3, 1>, sm);
     case 15: return occupancy_of(pair_fp32_kernel<4, 4, 2>, sm);
     case 16: return occupancy_of(pair_fp32_kernel<2, 6, 2>, sm);
+    case 17: return occupancy_of(pair_fp32_kernel<3, 4, 1>, sm);
     default: return occupancy_of(pair_fp32_kernel<4, 4, 0>, sm);
     }
 }
@@ -816,6 +819,7 @@ int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStr
         case 14: pair_fp32_kernel<4, 3, 1><<<grid, kThreads, sm, st>>>(a); break;
         case 15: pair_fp32_kernel<4, 4, 2><<<grid, kThreads, sm, st>>>(a); break;
         case 16: pair_fp32_kernel<2, 6, 2><<<grid, kThreads, sm, st>>>(a); break;
+        case 17: pair_fp32_kernel<3, 4, 1><<<grid, kThreads, sm, st>>>(a); break;
         default: pair_fp32_kernel<4, 4, 0><<<grid, kThreads, sm, st>>>(a); break;
         }
     }

@@ -226,7 +226,7 @@ def test_tensor_core_fit_matches_fp64_fit(small_periodic, grounded_small):
 
 
 # every blocking of the FP32 pair kernel the autotuner may pick
-PAIR_VARIANTS = [4, 5, 2, 12, 13, 14, 15, 16]
+PAIR_VARIANTS = [4, 5, 2, 12, 13, 14, 15, 16, 17]
 
 
 @pytest.mark.parametrize("variant", PAIR_VARIANTS)

@@ -1369,11 +1369,13 @@ int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_p
     const hsma_tuning value0 = pl->tune_value;
     std::vector<double> energies(nsys);
     std::vector<hsma_tuning> cands;
-    const int variants[9] = {4, 5, 2, 12, 13, 14, 15, 16, 17};
+    // candidates: the packed variants and the two-target scalar loop for
+    // reference (4, 5, 15, 16 never won on this part; they stay selectable)
+    const int variants[5] = {14, 17, 12, 13, 2};
     const int items[4] = {8, 16, 24, 48};
-    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 9); ++v)
+    for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 5); ++v)
         for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
-    hsma_tuning win{4, 24, 1e300};
+    hsma_tuning win{14, 48, 1e300};
     int rc = HSMA_OK;
     for (auto &c : cands) {
         pl->tune_fixed = true;

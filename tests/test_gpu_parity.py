@@ -260,6 +260,31 @@ def test_pair_variants_against_oracle(small_periodic, grounded_small, variant):
         assert_within(errors(F.cpu().numpy(), reft["forces"], U, reft["energy"]), "fp32", f"n=514 variant {variant}")
 
 
+def test_noncubic_periodic_box_and_wrapping():
+    """A periodic box with unequal sides (1.0 x 1.3 x 0.8, Rs = sqrt(3) R0:
+    two image shells along z, 75 shifts) against the oracle in FP64 and FP32;
+    and periodic input outside [0, L) (whole periods added and subtracted)
+    gives the result of the wrapped input."""
+    box = (1.0, 1.3, 0.8)
+    from oracle import hsma as oh
+    Rs = oh.alpha_to_rs(box, 3.0 ** 0.5)
+    w = I.Workload("noncubic", box, I.PERIODIC, 8, Rs, 2000, 600)
+    xyz, q = I.uniform_pm1(800, box, seed_offset=90)
+    ref, _ = oracle_run(xyz, q, w)
+    shifted = xyz + np.asarray(box) * np.random.default_rng(91).integers(-2, 3, size=xyz.shape)
+    for prec in ("fp64", "fp32"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            assert plan.info()["n_shifts"] == 75
+            U, F, pot, ns = plan.energy_forces(*to_dev(xyz, q), potentials=True)
+            assert ns == ref["n_inset"]
+            e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+            assert_within(e, prec, f"non-cubic {prec}")
+            Us, Fs, _, ns2 = plan.energy_forces(*to_dev(shifted, q))
+            assert ns2 == ns
+            assert abs(Us - U) <= (1e-12 if prec == "fp64" else 1e-7) * abs(U)
+            assert rms(Fs.cpu().numpy() - F.cpu().numpy()) <= (1e-10 if prec == "fp64" else 1e-6) * rms(F.cpu().numpy())
+
+
 def test_error_codes():
     hsma = hs()
     w = I.SMALL_PERIODIC

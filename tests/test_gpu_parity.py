@@ -321,6 +321,42 @@ def test_error_codes():
         hsma.Plan((1, 1, 1), 0, 8, 1.5, 2000, 10)  # fewer monitoring points than columns
 
 
+def test_empty_input_and_single_grounded_charge():
+    """Degenerate inputs: an empty system is an argument error (alone or
+    inside a batch) and leaves the plan usable; one charge in a grounded box,
+    whose only partners are its own images, matches the oracle and the exact
+    doubled-cell lattice."""
+    from oracle import checks
+    hsma = hs()
+    w = I.SMALL_PERIODIC
+    xyz, q = I.small_periodic()
+    with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces(np.zeros((0, 3)), np.zeros(0))
+        assert ei.value.code == -1
+        both_x = np.concatenate([xyz, xyz])
+        both_q = np.concatenate([q, q])
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces_batched(*to_dev(both_x, both_q), [0, len(q), len(q), 2 * len(q)])
+        assert ei.value.code == -1
+        U, _, _, _ = plan.energy_forces(*to_dev(xyz, q))
+        assert np.isfinite(U)
+    g = I.Workload("grounded-one", (1.0, 1.0, 1.0), I.GROUNDED, 12, 1.5, 6000, 1500)
+    x1 = np.array([[0.31, 0.62, 0.45]])
+    q1 = np.array([1.0])
+    ref, _ = oracle_run(x1, q1, g)
+    _, fld, U_exact = checks.grounded_box_exact(x1, q1, np.array(g.box))
+    for prec in ("fp64", "fp32"):
+        with hsma.Plan(g.box, g.bc, g.p, g.R, g.Q, g.Kmon, precision=prec) as plan:
+            U, F, pot, ns = plan.energy_forces(*to_dev(x1, q1), potentials=True)
+            assert ns == ref["n_inset"]
+            e = errors(F.cpu().numpy(), ref["forces"], U, ref["energy"], pot.cpu().numpy(), ref["pot"])
+            assert_within(e, prec, f"one grounded charge {prec}")
+            # the method's own accuracy against the exact image lattice
+            assert abs(U - U_exact) <= 1e-6 * abs(U_exact), (prec, U, U_exact)
+            assert np.abs(F.cpu().numpy()[0] - q1[0] * fld[0]).max() <= 1e-4 * np.abs(fld[0]).max()
+
+
 def test_batched_matches_single_and_oracle():
     w = I.BATCH_PERIODIC
     sizes = [600, 1000, 1500, 2048, 333 * 2]

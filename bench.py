@@ -45,6 +45,7 @@ OPS_SURFACE = 45                 # FP32 lane instructions per particle-direction
 
 
 def parse():
+    """Command-line options (the contract's --gpus/--steps/--warmup, --impl, workloads and tuning)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -376,6 +377,7 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
 
 
 def dist_env():
+    """RANK, WORLD_SIZE and LOCAL_RANK from the environment (torchrun), defaults for one process."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -384,6 +386,7 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi sampling of SM clocks, power and throttle reasons during the timed region."""
     def __init__(self):
         self.path = None
         self.proc = None
@@ -489,6 +492,7 @@ def reference_arm(args, rank, world):
 
 # ------------------------------------------------------------------ ours
 def main():
+    """The benchmark: one JSON line on rank 0."""
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":

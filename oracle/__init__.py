@@ -36,6 +36,7 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle's C library (compiled on first use)."""
     global _lib
     with _lock:
         if _lib is None:
@@ -90,6 +91,7 @@ def _ptr(a, t=_dp):
 # --------------------------------------------------------------------------
 
 def num_shells(Rs: float, La: float) -> int:
+    """Image shells needed along an axis: the smallest K with (K + 1/2) L >= Rs (in-set of Sec. II.A)."""
     return int(lib().hsmo_num_shells(float(Rs), float(La)))
 
 
@@ -127,6 +129,7 @@ def coulomb(sxyz, sq, txyz, tskip=None, field: bool = True, nthreads: int = 1):
 
 
 def basis(pts, P: int, Rs: float):
+    """Real solid harmonics r^n P_n^m cos/sin(m phi) scaled by Rs^-n at points (Eq. "harmonic"), unnormalised."""
     pts = _d(pts).reshape(-1, 3)
     out = np.empty((pts.shape[0], (P + 1) ** 2))
     lib().hsmo_basis(pts.shape[0], _ptr(pts), int(P), float(Rs), _ptr(out))
@@ -134,6 +137,7 @@ def basis(pts, P: int, Rs: float):
 
 
 def lstsq(A, b):
+    """Least squares min ||A x - b|| by column-equilibrated Householder QR; returns x and R's diagonal."""
     A = _d(A)
     b = _d(b)
     m, n = A.shape
@@ -146,12 +150,14 @@ def lstsq(A, b):
 
 
 def monitor_sphere(nm: int, R0: float):
+    """Fibonacci latitude grid of nm points on the sphere of radius R0 (monitoring points, Sec. II.A)."""
     out = np.empty((nm, 3))
     lib().hsmo_monitor_sphere(int(nm), float(R0), _ptr(out))
     return out
 
 
 def wrap_into_box(pts, L):
+    """Nearest periodic image inside the centred box (the partner x~ of a monitoring point, Sec. II.A)."""
     pts = _d(pts).reshape(-1, 3)
     L = _d(L)
     out = np.empty_like(pts)
@@ -160,6 +166,7 @@ def wrap_into_box(pts, L):
 
 
 def monitor_faces(K: int, L):
+    """About K points on the walls of a grounded box, split by area (monitoring points, Sec. II.A)."""
     L = _d(L)
     out = np.empty((K, 3))
     k = lib().hsmo_monitor_faces(int(K), _ptr(L), _ptr(out))
@@ -167,6 +174,7 @@ def monitor_faces(K: int, L):
 
 
 def quadrature(F2: int, F1: int, R: float):
+    """Fibonacci integration nodes (unit directions) and weights on the sphere of radius R (Sec. II.B)."""
     n = 2 * (F2 + 1)
     dirs = np.empty((n, 3))
     w = np.empty(n)

@@ -38,6 +38,7 @@ GROUNDED = 1
 
 
 def fibonacci_numbers(limit: int = 10**7):
+    """Fibonacci numbers 1, 2, 3, 5, ... up to limit (the F2 candidates of Sec. II.B)."""
     a, b = 1, 2
     out = [1, 2]
     while b < limit:
@@ -59,6 +60,7 @@ def fib_from_points(Q: int):
 
 
 def fib_predecessor(F2: int) -> int:
+    """F1: the Fibonacci number before F2 (azimuth step of the Fibonacci integration, Sec. II.B)."""
     fib = fibonacci_numbers(F2 + 1)
     if F2 not in fib:
         raise ValueError("F2 must be a Fibonacci number")
@@ -73,6 +75,7 @@ def degree_of_index(nb: int):
 
 @dataclass
 class Plan:
+    """Matrices and point sets of the preparation step (Sec. II.C, Table I upper half)."""
     box: np.ndarray
     bc: int
     P: int

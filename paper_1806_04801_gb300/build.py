@@ -25,6 +25,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 
 
 def nvcc() -> str:
+    """Path of nvcc (PATH, else /usr/local/cuda/bin); raises if the CUDA toolkit is missing."""
     cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(cand):
         raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libhsma")

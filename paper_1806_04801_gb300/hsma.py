@@ -22,6 +22,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32_ACC64, "fp32_tc": FP32_TC_FIT}
 
 
 class HsmaError(RuntimeError):
+    """A negative return code of the C ABI, with its hsma_strerror text."""
     def __init__(self, code: int, where: str):
         self.code = code
         msg = _lib().hsma_strerror(code).decode() if _LIB is not None else str(code)
@@ -29,26 +30,31 @@ class HsmaError(RuntimeError):
 
 
 class hsma_opts(ctypes.Structure):
+    """Mirror of hsma_opts (include/hsma.h)."""
     _fields_ = [("precision", ctypes.c_int), ("dr_rel", ctypes.c_double), ("fib_F2", ctypes.c_int),
                 ("far_field", ctypes.c_int), ("stream", ctypes.c_void_p), ("use_graphs", ctypes.c_int),
                 ("profile", ctypes.c_int)]
 
 
 class hsma_particles(ctypes.Structure):
+    """Mirror of hsma_particles (include/hsma.h)."""
     _fields_ = [("n", ctypes.c_int64), ("xyz", ctypes.c_void_p), ("q", ctypes.c_void_p),
                 ("on_device", ctypes.c_int)]
 
 
 class hsma_out(ctypes.Structure):
+    """Mirror of hsma_out (include/hsma.h)."""
     _fields_ = [("energy", ctypes.c_double), ("forces", ctypes.c_void_p), ("potentials", ctypes.c_void_p),
                 ("n_inset", ctypes.c_int64), ("n_images", ctypes.c_int)]
 
 
 class hsma_tuning(ctypes.Structure):
+    """Mirror of hsma_tuning (include/hsma.h)."""
     _fields_ = [("pair_variant", ctypes.c_int), ("items_per_slot", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class hsma_plan_info_t(ctypes.Structure):
+    """Mirror of hsma_plan_info_t (include/hsma.h)."""
     _fields_ = [("bc", ctypes.c_int), ("p", ctypes.c_int), ("n_basis", ctypes.c_int), ("n_cols", ctypes.c_int),
                 ("Kmon", ctypes.c_int), ("n_mon_targets", ctypes.c_int), ("F2", ctypes.c_int),
                 ("F1", ctypes.c_int), ("n_images", ctypes.c_int), ("n_shifts", ctypes.c_int),
@@ -141,6 +147,7 @@ def _stream_handle(stream):
 
 
 def kernel_launches() -> int:
+    """hsma_kernel_launches: kernels this library has launched (graph nodes counted on replay)."""
     return int(_lib().hsma_kernel_launches())
 
 
@@ -155,10 +162,12 @@ def fp32_peak() -> tuple:
 
 
 def version() -> str:
+    """hsma_version."""
     return _lib().hsma_version().decode()
 
 
 def strerror(code: int) -> str:
+    """hsma_strerror: the message of a return code."""
     return _lib().hsma_strerror(int(code)).decode()
 
 
@@ -190,27 +199,33 @@ class Plan:
     # ------------------------------------------------------------- info
     @property
     def handle(self):
+        """The opaque hsma_plan_t."""
         return self._h
 
     def info(self) -> dict:
+        """hsma_plan_get_info: sizes the plan chose (F2, N_o, monitoring targets, shifts, ...)."""
         i = hsma_plan_info_t()
         _check(_lib().hsma_plan_get_info(self._h, ctypes.byref(i)), "hsma_plan_get_info")
         return {k: getattr(i, k) for k, _ in hsma_plan_info_t._fields_}
 
     def set_stream(self, stream):
+        """hsma_plan_set_stream: the CUDA stream of later calls (torch stream or handle)."""
         _check(_lib().hsma_plan_set_stream(self._h, _stream_handle(stream)), "hsma_plan_set_stream")
 
     def set_precision(self, precision):
+        """hsma_plan_set_precision: "fp64", "fp32" or "fp32_tc" for later calls."""
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         _check(_lib().hsma_plan_set_precision(self._h, int(precision)), "hsma_plan_set_precision")
 
     def footprint(self, n: int) -> int:
+        """hsma_plan_footprint: device bytes one call with n particles needs."""
         b = ctypes.c_size_t()
         _check(_lib().hsma_plan_footprint(self._h, int(n), ctypes.byref(b)), "hsma_plan_footprint")
         return int(b.value)
 
     def get_matrix(self, which: int) -> np.ndarray:
+        """hsma_plan_get_matrix: a plan matrix copied to the host (see the header)."""
         info = self.info()
         shapes = {0: (info["n_mon_targets"], 3), 1: (info["Kmon"], info["n_cols"]),
                   2: (info["n_cols"], info["Kmon"]), 3: (2 * (info["F2"] + 1), 3), 4: (2 * (info["F2"] + 1),),
@@ -220,6 +235,7 @@ class Plan:
         return out
 
     def last_get(self, which: int, count: int) -> np.ndarray:
+        """hsma_last_get: an intermediate of the last update (A, b, Phi_in, Phi_out)."""
         out = np.empty(count)
         n = _lib().hsma_last_get(self._h, int(which), out.ctypes.data, count)
         if n < 0:
@@ -227,6 +243,7 @@ class Plan:
         return out[:n]
 
     def last_timings(self) -> list:
+        """hsma_last_timings: per-phase device milliseconds of the last update (profile plans)."""
         ms = np.zeros(8)
         n = _lib().hsma_last_timings(self._h, ms.ctypes.data, 8)
         if n < 0:
@@ -339,6 +356,7 @@ class Plan:
         _check(_lib().hsma_plan_set_tuning(self._h, ctypes.byref(t)), "hsma_plan_set_tuning")
 
     def get_tuning(self, offsets) -> dict:
+        """hsma_plan_get_tuning: the tuning a call with these offsets would use."""
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         t = hsma_tuning()
         _check(_lib().hsma_plan_get_tuning(self._h, off.shape[0] - 1, off.ctypes.data, ctypes.byref(t)),
@@ -358,12 +376,14 @@ class Plan:
         return {"pair_variant": t.pair_variant, "items_per_slot": t.items_per_slot, "ms": t.ms}
 
     def load_tuning(self, cache_path) -> int:
+        """hsma_plan_load_tuning: entries of an autotuner cache matching this plan; returns how many."""
         r = _lib().hsma_plan_load_tuning(self._h, str(cache_path).encode())
         if r < 0:
             raise HsmaError(r, "hsma_plan_load_tuning")
         return int(r)
 
     def close(self):
+        """hsma_plan_destroy (idempotent)."""
         if getattr(self, "_h", None):
             _lib().hsma_plan_destroy(self._h)
             self._h = None
@@ -434,16 +454,19 @@ def basis(pts, p: int, Rs: float, stream=None):
 
 # ------------------------------------------------------------------ serving
 class hsma_server_opts(ctypes.Structure):
+    """Mirror of hsma_server_opts (include/hsma.h)."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("lanes", ctypes.c_int),
                 ("precision", ctypes.c_int)]
 
 
 class hsma_request_info(ctypes.Structure):
+    """Mirror of hsma_request_info (include/hsma.h)."""
     _fields_ = [("n", ctypes.c_int64), ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
                 ("batch_size", ctypes.c_int), ("status", ctypes.c_int)]
 
 
 class hsma_server_stats_t(ctypes.Structure):
+    """Mirror of hsma_server_stats_t (include/hsma.h)."""
     _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
                 ("queued", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("elapsed_s", ctypes.c_double),
@@ -481,6 +504,7 @@ class Server:
         self._h = h
 
     def submit(self, xyz: np.ndarray, q: np.ndarray) -> int:
+        """hsma_server_submit: queue one configuration (host arrays); returns its ticket."""
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         q = np.ascontiguousarray(q, dtype=np.float64)
         t = ctypes.c_int64()
@@ -503,6 +527,7 @@ class Server:
         return int(_lib().hsma_server_cancel(self._h, int(ticket)))
 
     def stats(self) -> dict:
+        """hsma_server_stats: counts of queued, running, completed, failed and cancelled requests."""
         st = hsma_server_stats_t()
         _check(_lib().hsma_server_stats(self._h, ctypes.byref(st)), "hsma_server_stats")
         return {k: getattr(st, k) for k, _ in hsma_server_stats_t._fields_}

@@ -49,6 +49,7 @@ SERVING_PERIODIC = Workload("serving-periodic-p10", (1.0, 1.0, 1.0), PERIODIC, 1
 
 
 def rng(seed_offset: int = 0) -> np.random.Generator:
+    """The PCG64 generator of seed 1806_04801 + seed_offset."""
     return np.random.default_rng(SEED_BASE + seed_offset)
 
 
@@ -90,6 +91,7 @@ def grounded_cavity(n: int = 20_000):
 
 
 def log_uniform_sizes(count: int, lo: int, hi: int, seed_offset: int):
+    """count sizes log-uniform in [lo, hi], rounded to integers and up to even."""
     g = rng(seed_offset)
     n = np.exp(g.uniform(math.log(lo), math.log(hi), size=count))
     n = np.round(n).astype(np.int64)

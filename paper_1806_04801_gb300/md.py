@@ -43,6 +43,7 @@ class VelocityVerlet:
         return u, f
 
     def kinetic(self) -> float:
+        """Kinetic energy sum m v^2 / 2 (FP64)."""
         return float(0.5 * (self.m * self.v * self.v).sum())
 
     def step(self, nsteps: int = 1):

@@ -30,9 +30,11 @@ class GpuBackend:
         self.plan = plan
 
     def near(self, xyz, q, part, nparts):
+        """Stage 1 on this rank's slice (hsma_shard_near): owned indices, Phi_in, E_in and the monitoring potentials."""
         return self.plan.shard_near(xyz, q, part, nparts)
 
     def far(self, xyz, q, phi_mon, part, nparts):
+        """Stage 3 on this rank's slice (hsma_shard_far) from the summed monitoring potentials."""
         return self.plan.shard_far(xyz, q, phi_mon, part, nparts)
 
 
@@ -47,13 +49,16 @@ class TorchComm:
 
     @property
     def rank(self):
+        """This process's rank in the process group."""
         return self.dist.get_rank(self.group)
 
     @property
     def size(self):
+        """Number of ranks."""
         return self.dist.get_world_size(self.group)
 
     def allreduce_sum(self, a):
+        """Element-wise sum of a numpy array over the ranks."""
         import torch
         t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64))
         if self.device is not None:

@@ -554,8 +554,11 @@ __global__ void series_field_kernel(const SysDesc *sys, int nsys, int P, double 
 // pre-multiplied by the normalisation and the reciprocals 1/(n - m) staged in
 // shared memory), the sums over n folded into double-float accumulators after
 // every m.  FP64 issue is slow on this part; this evaluates the fitted
-// series at O(N N_b) FP32 cost.
-constexpr int kSeriesMaxP = 40;
+// series at O(N N_b) FP32 cost.  Pi_m^m = (2m - 1)!! leaves the FP32 range
+// near m = 29 (57!! ~ 6.5e38) and the normalisation nears FP32's smallest
+// normal number there, so orders above the paper's largest (P = 25) take the
+// FP64 kernel.
+constexpr int kSeriesMaxP = 25;
 __global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, double inv_rs, const double *norm,
                                          const double *A, const float4 *src_hi, const float4 *src_lo,
                                          double *phi_out, double *e_out)

@@ -481,6 +481,34 @@ def test_series_far_field(bc):
     assert abs(Ui - U) <= 1e-7 * abs(U)
 
 
+@pytest.mark.parametrize("P", [25, 30])
+def test_series_far_field_high_order(P):
+    """The series far field at high harmonic order: the FP32 kernel serves
+    orders up to the paper's largest (P = 25), the FP64 kernel above it
+    (where (2m - 1)!! leaves the FP32 range); both agree with the FP64 path's
+    series and with the surface images of the same plan."""
+    w = I.Workload(f"series-p{P}", (1.0, 1.0, 1.0), I.PERIODIC, P, 2.0 * 0.5 * 3.0 ** 0.5, 6000, 2 * (P + 1) ** 2)
+    xyz, q = I.random_neutral(256, w.box, seed_offset=60 + P)
+    dx, dq = to_dev(xyz, q)
+    out = {}
+    for prec, far in (("fp64", "series"), ("fp32", "series"), ("fp32", "images")):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec, far_field=far) as plan:
+            U, F, _, _ = plan.energy_forces(dx, dq)
+            F = F.cpu().numpy()
+            assert np.isfinite(U) and np.all(np.isfinite(F)), (prec, far)
+            out[(prec, far)] = (U, F)
+    U64, F64 = out[("fp64", "series")]
+    # the FP32 series against the FP64 series: the reduced-form bar
+    Us, Fs = out[("fp32", "series")]
+    assert rel_energy_err(Us, U64, q) <= 1e-6, (Us, U64)
+    assert rms(Fs - F64) <= 1e-5 * rms(F64)
+    # the surface images add the quadrature's error for harmonics up to
+    # degree P (N_o = 5928 directions): a looser, method-level bound
+    Ui, Fi = out[("fp32", "images")]
+    assert rel_energy_err(Ui, U64, q) <= 1e-5, (Ui, U64)
+    assert rms(Fi - F64) <= 1e-4 * rms(F64)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("bc", ["periodic", "grounded"])
 def test_target_sharded_stages(prec, bc):

@@ -225,6 +225,25 @@ def test_tensor_core_fit_matches_fp64_fit(small_periodic, grounded_small):
         assert rel_energy_err(E["fp32_tc"][i], E["fp32"][i], systems[i][1]) <= 5e-7, i
 
 
+def test_tensor_core_fit_high_order():
+    """The tensor-core fit at the paper's largest order (P = 25: M+ is
+    675 x 1250, six M tiles of the tcgen05 product, K split over 20 CTAs) on a
+    random-sign lattice, against the same plan with the FP64 fit."""
+    xyz, q = I.lattice_random_sign(10, 1.0, seed_offset=510)
+    P = 25
+    w = I.Workload("lattice-p25", (1.0, 1.0, 1.0), I.PERIODIC, P, 2.0 * 0.5 * 3.0 ** 0.5, 6000, 2 * P * P)
+    dx, dq = to_dev(xyz, q)
+    res = {}
+    for prec in ("fp32", "fp32_tc"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            U, F, _, _ = plan.energy_forces(dx, dq)
+            res[prec] = (U, F.cpu().numpy(), plan.last_get(0, (P + 1) ** 2))
+    (U32, F32, A32), (Utc, Ftc, Atc) = res["fp32"], res["fp32_tc"]
+    assert np.all(np.isfinite(Atc))
+    assert rel_energy_err(Utc, U32, q) <= 1e-6, (Utc, U32)
+    assert rms(Ftc - F32) <= 1e-5 * rms(F32)
+
+
 # every blocking of the FP32 pair kernel the autotuner may pick
 PAIR_VARIANTS = [4, 5, 2, 12, 13, 14, 15, 16, 17]
 

@@ -75,6 +75,8 @@ struct Workspace {
     float *tc_work = nullptr;
     long long *idx64 = nullptr;                     // target sharding: caller indices of a slice
     double4_32a *cen = nullptr;                     // in-set scratch: centred particles, spatial order
+    float4 *cenf = nullptr;                         // the same in FP32
+    double2 *qsums = nullptr;                       // per particle block: (sum q, sum |q|)
 };
 
 struct BatchShape {
@@ -373,6 +375,8 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
                                                   : nullptr;
     w->idx64 = c.take<long long>(sh.n_total);
     w->cen = c.take<double4_32a>(sh.n_total);
+    w->cenf = c.take<float4>(sh.n_total);
+    w->qsums = c.take<double2>(sh.cnt_total / std::max(1, p->nshifts) + 1);
     return align_up(c.off, 256);
 }
 
@@ -470,6 +474,8 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     ia.src64 = w.src64;
     ia.status = w.status;
     ia.cen = w.cen;
+    ia.cenf = w.cenf;
+    ia.qsums = w.qsums;
     if ((rc = launch_inset(ia, st))) return rc;
     const int TB = pair_targets_per_block(prec, sh.variant);
     if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
@@ -817,6 +823,8 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
     ia.src64 = w.src64;
     ia.status = w.status;
     ia.cen = w.cen;
+    ia.cenf = w.cenf;
+    ia.qsums = w.qsums;
     if ((rc = launch_inset(ia, st))) return rc;
 
     const long long cnt = t_hi - t_lo;

@@ -295,6 +295,8 @@ struct InsetArgs {
     double4_32a *src64;
     int *status;
     double4_32a *cen;       // [n] scratch: centred (x, y, z, q) in spatial order
+    float4 *cenf;           // [n] the same rounded to FP32 (the guarded in-sphere test)
+    double2 *qsums;         // [blocks] per particle block: (sum q, sum |q|)
 };
 int launch_inset(const InsetArgs &a, cudaStream_t st);
 

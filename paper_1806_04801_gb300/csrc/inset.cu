@@ -8,7 +8,8 @@
 // then the other shifts in the order of the shift table, each over the
 // particles in spatial order:
 //   centre  : per particle (spatial order) the centred, wrapped position and
-//             charge, once (the FP64 wrap is not repeated for every shift);
+//             charge, once (the FP64 wrap is not repeated for every shift),
+//             an FP32 copy and per-block charge sums;
 //   count   : per (system, shift, block of particles) the number of hits;
 //   scan    : per system, exclusive prefix over (shift, block) + totals, and
 //             the neutrality check of periodic systems;
@@ -72,13 +73,23 @@ __device__ __forceinline__ bool image_of(const Centred &c, int4 s, const Geometr
 
 __global__ void __launch_bounds__(kInsetThreads) inset_centre_kernel(InsetArgs a)
 {
+    __shared__ double red[32];
     int sys_i = blockIdx.y;
     const SysDesc sd = a.sys[sys_i];
+    if (blockIdx.x >= sd.nblk) return;
     long long j = (long long)blockIdx.x * kInsetThreads + threadIdx.x;
-    if (blockIdx.x >= sd.nblk || j >= sd.n) return;
-    Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
-    if (!c.ok) atomicOr(&a.status[sys_i], ST_OUT_OF_BOX);
-    a.cen[sd.part_off + j] = make_double4_32a(c.x, c.y, c.z, c.q);
+    double qv = 0.0;
+    if (j < sd.n) {
+        Centred c = load_centred(a.xyz, a.q, sd.part_off + a.perm[sd.part_off + j], a.g);
+        if (!c.ok) atomicOr(&a.status[sys_i], ST_OUT_OF_BOX);
+        a.cen[sd.part_off + j] = make_double4_32a(c.x, c.y, c.z, c.q);
+        a.cenf[sd.part_off + j] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.f);
+        qv = c.q;
+    }
+    // per-block charge sums for the neutrality check (fixed reduction order)
+    const double s = block_sum(qv, red);
+    const double sa = block_sum(fabs(qv), red);
+    if (threadIdx.x == 0) a.qsums[sd.cnt_off / a.n_shifts + blockIdx.x] = make_double2(s, sa);
 }
 
 __device__ __forceinline__ Centred centred_at(const InsetArgs &a, const SysDesc &sd, long long j)
@@ -93,6 +104,36 @@ __device__ __forceinline__ Centred centred_at(const InsetArgs &a, const SysDesc 
     return c;
 }
 
+// Membership of the image of particle j under a shift: decided in FP32 when
+// |r|^2 is clearly inside or outside the sphere, else by the FP64 test of
+// image_of (the reference predicate).  Near the sphere each coordinate is
+// at most Rs and carries at most three FP32 roundings of terms no larger
+// than Rs + max L, so the FP32 |r|^2 is within about 2e-6 (Rs + max L)^2 of
+// the exact one; the band, 1e-4 (Rs + max L)^2, is fifty times wider and
+// every decision taken in FP32 equals the FP64 one.
+__device__ __forceinline__ bool in_set(const InsetArgs &a, const SysDesc &sd, long long j, int4 s)
+{
+    if (s.x == 0 && s.y == 0 && s.z == 0) return true;
+    const float4 c = a.cenf[sd.part_off + j];
+    float sx = 1.f, sy = 1.f, sz = 1.f;
+    if (a.g.bc == HSMA_BC_GROUNDED) {
+        if (s.x & 1) sx = -1.f;
+        if (s.y & 1) sy = -1.f;
+        if (s.z & 1) sz = -1.f;
+    }
+    const float x = fmaf(sx, c.x, (float)s.x * (float)a.g.L[0]);
+    const float y = fmaf(sy, c.y, (float)s.y * (float)a.g.L[1]);
+    const float z = fmaf(sz, c.z, (float)s.z * (float)a.g.L[2]);
+    const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+    const double lmax = fmax(a.g.L[0], fmax(a.g.L[1], a.g.L[2]));
+    const float band = (float)(1e-4 * (a.g.Rs + lmax) * (a.g.Rs + lmax));
+    const float rs2 = (float)(a.g.Rs * a.g.Rs);
+    if (r2 < rs2 - band) return true;
+    if (r2 > rs2 + band) return false;
+    double dx, dy, dz, dq;
+    return image_of(centred_at(a, sd, j), s, a.g, dx, dy, dz, dq);
+}
+
 __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
 {
     int sys_i = blockIdx.z;
@@ -102,11 +143,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_count_kernel(InsetArgs a)
     int sh = blockIdx.y;
     long long j = (long long)blk * kInsetThreads + threadIdx.x;
     int hit = 0;
-    if (j < sd.n) {
-        Centred c = centred_at(a, sd, j);
-        double x, y, z, q;
-        hit = image_of(c, a.shifts[sh], a.g, x, y, z, q) ? 1 : 0;
-    }
+    if (j < sd.n) hit = in_set(a, sd, j, a.shifts[sh]) ? 1 : 0;
     int cnt = __syncthreads_count(hit);
     if (threadIdx.x == 0) a.counts[sd.cnt_off + (long long)sh * sd.nblk + blk] = cnt;
 }
@@ -120,12 +157,13 @@ __global__ void __launch_bounds__(1024) inset_scan_kernel(InsetArgs a)
     const SysDesc sd = a.sys[sys_i];
     const long long total = block_scan_inplace(a.counts + sd.cnt_off, (long long)a.n_shifts * sd.nblk, wsum, &carry);
     if (threadIdx.x == 0) a.ns[sys_i] = total;
-    // neutrality of periodic systems: |sum q| <= 1e-12 sum |q| (deterministic order)
+    // neutrality of periodic systems: |sum q| <= 1e-12 sum |q|, from the
+    // per-block sums in block order (deterministic)
     double s = 0.0, sa = 0.0;
-    for (long long j = threadIdx.x; j < sd.n; j += blockDim.x) {
-        double qq = a.q[sd.part_off + j];
-        s += qq;
-        sa += fabs(qq);
+    const double2 *qs = a.qsums + sd.cnt_off / a.n_shifts;
+    for (int b = threadIdx.x; b < sd.nblk; b += blockDim.x) {
+        s += qs[b].x;
+        sa += qs[b].y;
     }
     s = block_sum(s, red);
     sa = block_sum(sa, red);
@@ -143,11 +181,7 @@ __global__ void __launch_bounds__(kInsetThreads) inset_scatter_kernel(InsetArgs 
     int sh = blockIdx.y;
     long long j = (long long)blk * kInsetThreads + threadIdx.x;
     bool hit = false;
-    double x = 0, y = 0, z = 0, q = 0;
-    if (j < sd.n) {
-        Centred c = centred_at(a, sd, j);
-        hit = image_of(c, a.shifts[sh], a.g, x, y, z, q);
-    }
+    if (j < sd.n) hit = in_set(a, sd, j, a.shifts[sh]);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned m = __ballot_sync(0xffffffffu, hit);
     if (lane == 0) wsum[wid] = __popc(m);
@@ -156,6 +190,9 @@ __global__ void __launch_bounds__(kInsetThreads) inset_scatter_kernel(InsetArgs 
     for (int w = 0; w < wid; ++w) before += wsum[w];
     before += __popc(m & ((1u << lane) - 1u));
     if (!hit) return;
+    // the image itself in FP64 (positions of the in-set are exact to FP64)
+    double x, y, z, q;
+    image_of(centred_at(a, sd, j), a.shifts[sh], a.g, x, y, z, q);
     long long slot = sd.src_off + a.counts[sd.cnt_off + (long long)sh * sd.nblk + blk] + before;
     if (a.src64) a.src64[slot] = make_double4_32a(x, y, z, q);
     if (a.src_hi) {

@@ -340,6 +340,61 @@ def test_error_codes():
         hsma.Plan((1, 1, 1), 0, 8, 1.5, 2000, 10)  # fewer monitoring points than columns
 
 
+def _near_sphere_sources(box, Rs, bc, deltas, seed):
+    """Sources (box frame) each with one image at |r| = Rs (1 + delta): the
+    image direction is a shift whose box lies about Rs away, tilted at
+    random, and the source is solved from image = S c + s L (S flips the odd
+    axes of a grounded shift), kept well inside the box."""
+    import itertools
+    rng = np.random.default_rng(seed)
+    L = np.asarray(box, dtype=np.float64)
+    cands = [np.array(s) for s in itertools.product(range(-3, 4), repeat=3)
+             if any(s) and abs(np.linalg.norm(np.array(s) * L) - Rs) < 0.3 * L.min()]
+    pts, want = [], []
+    for d in deltas:
+        while True:
+            s = cands[rng.integers(len(cands))]
+            u = s * L + rng.normal(scale=0.05, size=3)
+            r = Rs * (1.0 + d) * u / np.linalg.norm(u)
+            S = np.where((s % 2 == 1) & (bc == I.GROUNDED), -1.0, 1.0)
+            c = S * (r - s * L)
+            if np.all(np.abs(c) < 0.45 * L):
+                break
+        pts.append(c + 0.5 * L)
+        want.append((S * c + s * L, d < 0))
+    return np.array(pts), want
+
+
+@pytest.mark.parametrize("bc", [I.PERIODIC, I.GROUNDED])
+def test_inset_membership_at_the_sphere(bc):
+    """Images within 1e-9 .. 1e-2 (relative) of the sphere |r| = Rs, on both
+    sides, inside and outside the band where the in-set test falls back from
+    FP32 to FP64: the in-set size and Phi_in at every particle (which moves
+    by O(1) if one image changes side) match the oracle."""
+    import oracle
+    box = (1.0, 1.0, 1.0)
+    w = I.Workload("near-sphere", box, bc, 8, 1.5, 2000, 600)
+    mags = [1e-2, 1e-3, 2e-4, 1e-4, 1e-5, 1e-6, 1e-7, 1e-9]
+    deltas = [sg * m for m in mags for sg in (1.0, -1.0)] * 2
+    xyz, want = _near_sphere_sources(box, w.R, bc, deltas, seed=1806)
+    n = len(xyz)
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    # the construction: each planned image sits on the side its delta says
+    c = xyz - 0.5 * np.asarray(box)
+    sx, _, _, _ = oracle.inset(c, q, np.asarray(box), bc, w.R)
+    for img, inside in want:
+        hit = np.any(np.all(np.abs(sx[n:] - img) <= 1e-12, axis=1))
+        assert hit == inside, (img, inside)
+    ref, _ = oracle_run(xyz, q, w)
+    for prec in PREC:
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            U, F, pot, ns = plan.energy_forces(*to_dev(xyz, q), potentials=True)
+            assert ns == ref["n_inset"], prec
+            phi_in = plan.last_get(3, n)
+            tol = 1e-12 if prec == "fp64" else 1e-6
+            assert rms(phi_in - ref["phi_in"]) <= tol * rms(ref["phi_in"]), prec
+
+
 def test_empty_input_and_single_grounded_charge():
     """Degenerate inputs: an empty system is an argument error (alone or
     inside a batch) and leaves the plan usable; one charge in a grounded box,

@@ -104,6 +104,45 @@ def test_monitor_faces():
     assert abs(nz - K * 2 / 10) <= 1
 
 
+def test_periodic_fit_on_box_faces_is_singular():
+    """Why the periodic monitoring points sit on the circumsphere (Sec. II.A):
+    with points on the box faces, each paired with its periodic partner on
+    the opposite face, every harmonic that is even in x, in y and in z takes
+    equal values at both points of each pair, so its column of the fitting
+    matrix Phi(x) - Phi(x~) vanishes and its coefficient is undetermined.
+    Which harmonics are even is found by reflecting random points, not from
+    the face matrix; the circumsphere matrix of the same order has full rank."""
+    L = np.array([1.0, 1.0, 1.0])
+    P, K, Rs = 8, 600, 1.5
+    g = np.random.default_rng(11)
+    # K points on the three lower faces (the upper ones are their partners)
+    pts = []
+    for a in range(3):
+        p = g.uniform(-0.5, 0.5, size=(K // 3, 3)) * L
+        p[:, a] = -0.5 * L[a]
+        pts.append(p)
+    x = np.concatenate(pts)
+    xt = oracle.wrap_into_box(x, L)
+    np.testing.assert_allclose(np.abs(x - xt).sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    M = (oracle.basis(x, P, Rs) - oracle.basis(xt, P, Rs))[:, 1:]
+    zero = np.abs(M).max(axis=0) <= 1e-13 * np.abs(M).max()
+    r = g.standard_normal((64, 3))
+    B = oracle.basis(r, P, Rs)
+    even = np.ones(B.shape[1], dtype=bool)
+    for a in range(3):
+        rr = r.copy()
+        rr[:, a] = -rr[:, a]
+        even &= np.abs(oracle.basis(rr, P, Rs) - B).max(axis=0) <= 1e-12 * np.abs(B).max()
+    assert np.array_equal(zero, even[1:])
+    assert zero.sum() >= 5
+    # the circumsphere placement: full column rank, well conditioned
+    xs = oracle.monitor_sphere(K, 0.5 * np.linalg.norm(L))
+    Ms = (oracle.basis(xs, P, Rs) - oracle.basis(oracle.wrap_into_box(xs, L), P, Rs))[:, 1:]
+    Ms = Ms / np.linalg.norm(Ms, axis=0)
+    sv = np.linalg.svd(Ms, compute_uv=False)
+    assert sv[0] / sv[-1] < 1e3
+
+
 # ---------------------------------------------------------------- in-set
 def test_num_shells_brute_force():
     for Rs, La in [(1.5, 1.0), (3.464, 2.0), (2.121, 1.0), (2.121, 2.0), (0.9, 1.0)]:

@@ -395,6 +395,31 @@ def test_inset_membership_at_the_sphere(bc):
             assert rms(phi_in - ref["phi_in"]) <= tol * rms(ref["phi_in"]), prec
 
 
+@pytest.mark.parametrize("scale", [7.3, 1000.0])
+def test_scale_invariance(scale):
+    """Gaussian units have no length scale: a box, sphere and positions all
+    scaled by s give U / s and F / s^2 (potentials / s).  Every plan length
+    (monitoring points, Rs, Delta r, images) scales with the box, so the two
+    runs differ by rounding only; at s = 1000 the FP32 path also shows that
+    its split (hi + lo) positions keep FP32 differences exact relative to
+    the box, not to the origin."""
+    w = I.SMALL_PERIODIC
+    xyz, q = I.small_periodic()
+    big = tuple(scale * b for b in w.box)
+    # two runs, each within the parity tolerance of the oracle
+    for prec, tol, ftol in (("fp64", 1e-11, 1e-11), ("fp32", 2e-6, 2e-5)):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as p1, \
+                hs().Plan(big, w.bc, w.p, scale * w.R, w.Q, w.Kmon, precision=prec) as ps:
+            U1, F1, pot1, n1 = p1.energy_forces(*to_dev(xyz, q), potentials=True)
+            Us, Fs, pots, ns = ps.energy_forces(*to_dev(scale * xyz, q), potentials=True)
+            assert ns == n1
+            assert abs(Us * scale - U1) <= tol * abs(U1), (prec, Us * scale, U1)
+            F1 = F1.cpu().numpy()
+            assert rms(Fs.cpu().numpy() * scale ** 2 - F1) <= ftol * rms(F1), prec
+            pot1 = pot1.cpu().numpy()
+            assert rms(pots.cpu().numpy() * scale - pot1) <= tol * rms(pot1), prec
+
+
 def test_empty_input_and_single_grounded_charge():
     """Degenerate inputs: an empty system is an argument error (alone or
     inside a batch) and leaves the plan usable; one charge in a grounded box,

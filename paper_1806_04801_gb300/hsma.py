@@ -22,9 +22,12 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32_ACC64, "fp32_tc": FP32_TC_FIT}
 
 
 class HsmaError(RuntimeError):
-    """A negative return code of the C ABI, with its hsma_strerror text."""
-    def __init__(self, code: int, where: str):
+    """A negative return code of the C ABI, with its hsma_strerror text.
+    ``status``: for a failed batched call, each system's own code (numpy
+    int32 array), else None."""
+    def __init__(self, code: int, where: str, status=None):
         self.code = code
+        self.status = status
         msg = _lib().hsma_strerror(code).decode() if _LIB is not None else str(code)
         super().__init__(f"{where}: {msg} (code {code})")
 
@@ -283,7 +286,8 @@ class Plan:
     def energy_forces_batched(self, xyz, q, offsets, forces=True, potentials=False):
         """hsma_energy_forces_batched over concatenated systems; offsets is a
         sequence of nsys+1 increasing integers.  Returns (energies, forces,
-        potentials, status)."""
+        potentials, status).  On an error the raised HsmaError carries the
+        per-system codes in its ``status``."""
         pxyz, dev = _ptr_and_dev(xyz)
         pq, _ = _ptr_and_dev(q)
         off = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -307,7 +311,8 @@ class Plan:
         rc = _lib().hsma_energy_forces_batched(self._h, nsys, off.ctypes.data, ctypes.byref(part), e.ctypes.data,
                                                _ptr_and_dev(f)[0] if f is not None else None,
                                                _ptr_and_dev(p)[0] if p is not None else None, st.ctypes.data)
-        _check(rc, "hsma_energy_forces_batched")
+        if rc != HSMA_OK:
+            raise HsmaError(rc, "hsma_energy_forces_batched", status=st)
         return e, f, p, st
 
     # ---------------------------------------------------- target sharding

@@ -479,6 +479,49 @@ def test_batched_matches_single_and_oracle():
                     assert_within(errors(F[sl], ref["forces"], E[i], ref["energy"]), prec, f"batched sys {i}")
 
 
+def test_batched_grounded_and_per_system_errors():
+    """Grounded cavities of ragged sizes in one batched call match the same
+    systems one by one (all three precisions) and the oracle (FP64); a batch
+    with one non-neutral periodic system fails with that system's code in
+    its slot and zeros elsewhere, and the plan serves the next batch."""
+    hsma = hs()
+    g = I.Workload("grounded-batch", (1.0, 1.0, 2.0), I.GROUNDED, 8, I.GROUNDED_CAVITY.R, 2000, 600)
+    sizes = [700, 1300, 257, 1024]
+    systems = [I.uniform_pm1(n, g.box, seed_offset=70 + i, margin=0.01) for i, n in enumerate(sizes)]
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])  # sizes rounded to even
+    ref, _ = oracle_run(*systems[2], g)
+    for prec in PREC:
+        with hsma.Plan(g.box, g.bc, g.p, g.R, g.Q, g.Kmon, precision=prec) as plan:
+            E, F, _, st = plan.energy_forces_batched(*to_dev(xyz, q), off)
+            F = F.cpu().numpy()
+            assert np.all(st == 0)
+            for i, (sx, sq) in enumerate(systems):
+                U1, F1, _, _ = plan.energy_forces(*to_dev(sx, sq))
+                F1 = F1.cpu().numpy()
+                sl = slice(off[i], off[i + 1])
+                assert abs(E[i] - U1) <= TOL[prec]["energy"] * abs(U1), (prec, i)
+                assert rms(F[sl] - F1) <= TOL[prec]["force_rms"] * rms(F1), (prec, i)
+            sl = slice(off[2], off[3])
+            assert_within(errors(F[sl], ref["forces"], E[2], ref["energy"]), prec, f"grounded batch {prec}")
+    w = I.SMALL_PERIODIC
+    per = [I.uniform_pm1(n, w.box, seed_offset=80 + i) for i, n in enumerate([500, 800, 600])]
+    bad_q = per[1][1].copy()
+    bad_q[0] += 1.0
+    xyz = np.concatenate([s[0] for s in per])
+    qb = np.concatenate([per[0][1], bad_q, per[2][1]])
+    qg = np.concatenate([s[1] for s in per])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in per])])
+    with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        with pytest.raises(hsma.HsmaError) as ei:
+            plan.energy_forces_batched(*to_dev(xyz, qb), off)
+        assert ei.value.code == -2
+        assert list(ei.value.status) == [0, -2, 0]
+        E, _, _, st = plan.energy_forces_batched(*to_dev(xyz, qg), off)
+        assert np.all(st == 0) and np.all(np.isfinite(E))
+
+
 @pytest.mark.slow
 def test_large_periodic_sampled_full_size():
     """The benchmarked workload at full size (100000 charges, p = 12): FP32 and

@@ -57,7 +57,8 @@ extern "C" {
 #define HSMA_E_ILLCOND (-8)      /* fitting matrix numerically rank deficient        */
 #define HSMA_E_NOT_FOUND (-9)    /* unknown ticket / item                            */
 #define HSMA_E_AGAIN (-10)       /* serving: result not ready yet                    */
-#define HSMA_E_CAPACITY (-11)    /* serving: request larger than the memory budget   */
+#define HSMA_E_CAPACITY (-11)    /* request larger than the serving memory budget or
+                                    the static scratch array                       */
 #define HSMA_E_CANCELLED (-12)   /* serving: request cancelled before it ran          */
 
 /* ------------------------------------------------------------ parameters */

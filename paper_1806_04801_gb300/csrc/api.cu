@@ -962,7 +962,7 @@ const char *hsma_strerror(int code)
         case HSMA_E_ILLCOND: return "fitting matrix is numerically rank deficient";
         case HSMA_E_NOT_FOUND: return "not found";
         case HSMA_E_AGAIN: return "not ready";
-        case HSMA_E_CAPACITY: return "request exceeds the memory budget";
+        case HSMA_E_CAPACITY: return "request exceeds the memory budget (serving) or the static scratch array";
         case HSMA_E_CANCELLED: return "request cancelled";
         default: return "unknown error";
     }
@@ -1278,7 +1278,7 @@ int hsma_energy_forces(hsma_plan_t pl, const hsma_particles *x, hsma_out *out)
 int hsma_energy_forces_batched(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_particles *all,
                                double *energies, double *forces, double *potentials, int *status)
 {
-    if (!pl || !all || nsys < 1 || !energies) return HSMA_E_ARG;
+    if (!pl || !all || nsys < 1 || !offsets || !energies) return HSMA_E_ARG;
     for (int s = 0; s < nsys; ++s)
         if (offsets[s + 1] <= offsets[s]) return HSMA_E_ARG;
     if (all->n != 0 && all->n != offsets[nsys]) return HSMA_E_ARG;

@@ -88,6 +88,7 @@ void lane_main(hsma_server_s *s, int lane)
                     s->queue.pop_front();
                     r->status = HSMA_E_CAPACITY;
                     r->t_done = Clock::now();
+                    r->t_start = r->t_done;
                     s->failed++;
                     s->cv_done.notify_all();
                     continue;

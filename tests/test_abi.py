@@ -64,3 +64,109 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(hsma, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         hsma.lib()
+
+
+def test_argument_errors_are_caught_before_any_device_work(lib):
+    """Every entry point validates its arguments on the host and returns
+    HSMA_E_ARG (or HSMA_E_CAPACITY for a direct sum beyond the static array)
+    before it touches the device, so these calls run without a GPU."""
+    from paper_1806_04801_gb300 import hsma
+    ARG, CAP = -1, -11
+    D3 = ctypes.c_double * 3
+    out = ctypes.c_void_p()
+    unit = D3(1.0, 1.0, 1.0)
+
+    def plan(box=unit, bc=0, p=8, R=1.5, Q=2000, K=600, **opt):
+        o = hsma.hsma_opts()
+        lib.hsma_opts_default(ctypes.byref(o))
+        for k, v in opt.items():
+            setattr(o, k, v)
+        return lib.hsma_plan(ctypes.byref(out), box, bc, p, R, Q, K, ctypes.byref(o))
+
+    assert lib.hsma_plan(None, unit, 0, 8, 1.5, 2000, 600, None) == ARG
+    assert lib.hsma_plan(ctypes.byref(out), None, 0, 8, 1.5, 2000, 600, None) == ARG
+    assert plan(box=D3(1.0, 0.0, 1.0)) == ARG             # empty box
+    assert plan(box=D3(1.0, -1.0, 1.0)) == ARG
+    assert plan(bc=2) == ARG                               # neither periodic nor grounded
+    assert plan(p=0) == ARG and plan(p=41) == ARG          # harmonic order out of range
+    assert plan(R=0.5 * 3 ** 0.5) == ARG                   # sphere must enclose the box
+    assert plan(R=float("nan")) == ARG and plan(R=float("inf")) == ARG
+    assert plan(K=79) == ARG                               # periodic p = 8: 80 fitted columns
+    assert plan(bc=1, K=80) == ARG                         # grounded p = 8: 81 columns
+    assert plan(K=16385) == ARG
+    assert plan(Q=11) == ARG                               # fewer surface points than the smallest rule
+    assert plan(fib_F2=100) == ARG                         # not a Fibonacci number
+    assert plan(precision=3) == ARG and plan(precision=-1) == ARG
+    assert plan(far_field=2) == ARG
+    assert out.value is None                               # no plan handed out
+
+    # update, sharding, tuning and inspection calls without a plan
+    parts = hsma.hsma_particles(0, None, None, 0)
+    res = hsma.hsma_out()
+    assert lib.hsma_energy_forces(None, ctypes.byref(parts), ctypes.byref(res)) == ARG
+    e = (ctypes.c_double * 2)()
+    off = (ctypes.c_int64 * 3)(0, 5, 9)
+    assert lib.hsma_energy_forces_batched(None, 2, off, ctypes.byref(parts), e, None, None, None) == ARG
+    cnt = ctypes.c_int64()
+    assert lib.hsma_shard_near(None, ctypes.byref(parts), 0, 1, None, None, None, ctypes.byref(cnt), None) == ARG
+    assert lib.hsma_shard_far(None, ctypes.byref(parts), None, 0, 1, None, None, None, ctypes.byref(cnt)) == ARG
+    tun = hsma.hsma_tuning(14, 48, 0.0)
+    assert lib.hsma_plan_set_tuning(None, ctypes.byref(tun)) == ARG
+    assert lib.hsma_plan_get_tuning(None, 2, off, ctypes.byref(tun)) == ARG
+    assert lib.hsma_autotune(None, 2, off, ctypes.byref(parts), None, ctypes.byref(tun)) == ARG
+    assert lib.hsma_plan_load_tuning(None, b"/nonexistent") == ARG
+    sz = ctypes.c_size_t()
+    assert lib.hsma_plan_footprint(None, 10, ctypes.byref(sz)) == ARG
+    info = hsma.hsma_plan_info_t()
+    assert lib.hsma_plan_get_info(None, ctypes.byref(info)) == ARG
+    assert lib.hsma_plan_set_precision(None, 0) == ARG
+    buf = (ctypes.c_double * 8)()
+    assert lib.hsma_plan_get_matrix(None, 0, buf, 8) == ARG
+    assert lib.hsma_last_timings(None, buf, 8) == ARG
+    assert lib.hsma_last_get(None, 0, buf, 8) == ARG
+    lib.hsma_plan_destroy(None)                            # a no-op
+
+    # direct sums and the basis: sizes, precision, alignment
+    src = (ctypes.c_double * 8)()
+    tgt = (ctypes.c_double * 6)()
+    pot = (ctypes.c_double * 2)()
+    for fn in (lib.hsma_coulomb_sum, lib.hsma_coulomb_sum_static):
+        assert fn(0, src, 2, tgt, pot, None, 1, None) == ARG
+        assert fn(2, src, 0, tgt, pot, None, 1, None) == ARG
+        assert fn(2, None, 2, tgt, pot, None, 1, None) == ARG
+        assert fn(2, src, 2, tgt, None, None, 1, None) == ARG
+        assert fn(2, src, 2, tgt, pot, None, 2, None) == ARG     # only FP64 or FP32 pair sums
+        misaligned = ctypes.c_void_p(ctypes.addressof(src) + 4)
+        assert fn(2, misaligned, 2, tgt, pot, None, 1, None) == ARG
+    assert lib.hsma_coulomb_sum(1 << 32, src, 2, tgt, pot, None, 1, None) == ARG
+    assert lib.hsma_coulomb_sum_static(1 << 32, src, 2, tgt, pot, None, 1, None) == CAP
+    assert lib.hsma_basis(-1, 1.0, 2, tgt, buf, None) == ARG
+    assert lib.hsma_basis(41, 1.0, 2, tgt, buf, None) == ARG
+    assert lib.hsma_basis(4, 0.0, 2, tgt, buf, None) == ARG
+    assert lib.hsma_basis(4, 1.0, 0, tgt, buf, None) == ARG
+    assert lib.hsma_fp32_peak(None, None) == ARG
+
+    # serving: options and handles
+    so = hsma.hsma_server_opts()
+    assert lib.hsma_server_opts_default(ctypes.byref(so)) == 0
+    assert so.max_batch == 64 and so.lanes == 2 and so.precision == hsma.FP32_ACC64
+    srv = ctypes.c_void_p()
+    for field, bad in (("lanes", 0), ("lanes", 17), ("max_batch", 0)):
+        o2 = hsma.hsma_server_opts()
+        lib.hsma_server_opts_default(ctypes.byref(o2))
+        setattr(o2, field, bad)
+        assert lib.hsma_server_create(ctypes.byref(srv), unit, 0, 8, 1.5, 2000, 600, ctypes.byref(o2)) == ARG
+    assert srv.value is None
+    t = ctypes.c_int64()
+    assert lib.hsma_server_submit(None, 2, src, pot, ctypes.byref(t)) == ARG
+    assert lib.hsma_server_cancel(None, 1) == ARG
+    assert lib.hsma_server_stats(None, None) == ARG
+
+
+def test_every_error_code_has_its_own_message(lib):
+    from paper_1806_04801_gb300 import hsma
+    msgs = [hsma.strerror(c) for c in range(-12, 1)]
+    assert len(set(msgs)) == len(msgs)
+    assert all(m != "unknown error" for m in msgs)
+    assert hsma.strerror(-13) == "unknown error" and hsma.strerror(7) == "unknown error"
+    assert "static scratch" in hsma.strerror(-11) and "memory budget" in hsma.strerror(-11)

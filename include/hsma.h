@@ -112,7 +112,9 @@ int hsma_opts_default(hsma_opts *opts);
  *   box   [L_x, L_y, L_z] > 0 (host pointer)
  *   bc    hsma_bc
  *   p     harmonic order P, 1 <= p <= 40; N_b = (p+1)^2 basis functions
- *   R     auxiliary sphere radius Rs; must exceed the circumradius of the box
+ *   R     auxiliary sphere radius Rs; must exceed the circumradius of the box,
+ *         and the image shifts k with |k_a| <= K_a, (K_a - 1/2) L_a < Rs <=
+ *         (K_a + 1/2) L_a, must number at most 65535
  *   Q     requested number of surface points (used when opts->fib_F2 == 0)
  *   Kmon  number of monitoring points, Kmon >= N_b, Kmon <= 16384
  *   opts  NULL for defaults
@@ -177,6 +179,8 @@ typedef struct {
  * A = M+ b, the surface images Q_j (Sec. II.B) and their potential and field
  * at the particles, energy and forces.  Returns after the energy is on the
  * host; forces/potentials are complete on return.
+ * Size limit: n * n_shifts < 2^31 (the in-set capacity of a system is
+ * 32-bit; n < 7.9e7 for the usual 27 shifts); larger n is HSMA_E_ARG.
  * Errors: HSMA_E_ARG, HSMA_E_NONNEUTRAL, HSMA_E_OUT_OF_BOX,
  * HSMA_E_COINCIDENT, HSMA_E_OOM, HSMA_E_TIMEOUT, HSMA_E_CUDA. */
 int hsma_energy_forces(hsma_plan_t plan, const hsma_particles *x_q, hsma_out *out);
@@ -187,7 +191,9 @@ int hsma_energy_forces(hsma_plan_t plan, const hsma_particles *x_q, hsma_out *ou
  * values, offsets[0] = 0).  energies: host array of nsys.  forces /
  * potentials: concatenated (offsets[nsys] x 3 / offsets[nsys]) in the same
  * memory space as *all, or NULL.  An error in one system fails the call;
- * status (host array of nsys, or NULL) receives each system's code. */
+ * status (host array of nsys, or NULL) receives each system's code.
+ * Size limits: nsys <= 65535 and, per system, those of hsma_energy_forces;
+ * beyond them HSMA_E_ARG. */
 int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offsets,
                                const hsma_particles *all, double *energies, double *forces,
                                double *potentials, int *status);

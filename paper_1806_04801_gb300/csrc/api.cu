@@ -36,6 +36,12 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kInsetBlock = 256;
+// Size limits of the update step.  Systems and image shifts index grid
+// dimensions y / z of several kernels (at most 65535 each); a system's in-set
+// slots, particle indices and work items are 32-bit.
+constexpr int kMaxSystems = 65535;
+constexpr int kMaxShifts = 65535;
+constexpr long long kMaxInsetSlots = (1LL << 31) - 1;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -181,8 +187,11 @@ bool fib_pred(int F2, int *F1)
     return false;
 }
 
+// Image shells per axis: the smallest k with (k + 1/2) L_a >= Rs.  A sphere
+// 1e5 box lengths across or more returns 1e5, far beyond any shift table.
 int shells(double Rs, double La)
 {
+    if (!(Rs / La < 1e5)) return 100000;
     int k = 0;
     while ((k + 1) * La - 0.5 * La < Rs) ++k;
     return k;
@@ -327,8 +336,8 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
     sh->hist_total = hist;
     sh->tiles_total = tiles;
     sh->max_tiles = max_tiles;
-    sh->items = (int)items;
-    sh->surf_items = (int)surf;
+    sh->items = items > INT32_MAX ? -1 : (int)items;
+    sh->surf_items = surf > INT32_MAX ? -1 : (int)surf;
     sh->nblk_max = nblk_max;
     sh->max_tgt = max_tgt;
 }
@@ -571,16 +580,17 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     if (!p || nsys < 1 || !offsets || !all || !all->xyz || !all->q) return HSMA_E_ARG;
     if (offsets[0] != 0) return HSMA_E_ARG;
     if (((uintptr_t)all->xyz | (uintptr_t)all->q | (uintptr_t)forces | (uintptr_t)pot) & 7) return HSMA_E_ARG;
+    if (nsys > kMaxSystems) return HSMA_E_ARG;
     std::vector<long long> n(nsys);
     for (int s = 0; s < nsys; ++s) {
         n[s] = offsets[s + 1] - offsets[s];
-        if (n[s] < 1) return HSMA_E_ARG;
+        if (n[s] < 1 || n[s] > kMaxInsetSlots / p->nshifts) return HSMA_E_ARG;
     }
     const int prec = p->precision;
     const bool on_dev = all->on_device != 0;
     BatchShape sh;
     shape_batch(p, nsys, n.data(), prec, choose_tuning(p, nsys, n.data()), &sh);
-    if (sh.items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
+    if (sh.items < 0 || sh.surf_items < 0 || sh.cap_total > (1LL << 40)) return HSMA_E_ARG;
     Workspace w;
     size_t need = carve_workspace(p, sh, prec, true, true, nullptr, &w);
     int rc = ensure_workspace(p, need);
@@ -752,9 +762,11 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
         return HSMA_E_ARG;
     if (far_stage ? !phi_mon_in : !phi_mon_out) return HSMA_E_ARG;
     const long long n = x->n;
+    if (n > kMaxInsetSlots / p->nshifts) return HSMA_E_ARG;
     const int prec = p->precision;
     BatchShape sh;
     shape_batch(p, 1, &n, prec, choose_tuning(p, 1, &n), &sh);
+    if (sh.items < 0 || sh.surf_items < 0) return HSMA_E_ARG;
     SysDesc &d = sh.sys[0];
     const int TB = pair_targets_per_block(prec, sh.variant);
     const int STB = surface_targets_per_block();
@@ -993,6 +1005,12 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     } else {
         if (Q < 12) return HSMA_E_ARG;
         fib_from_q(Q, &F2, &F1);
+    }
+
+    {
+        long long nsh = 1;
+        for (int a = 0; a < 3; ++a) nsh *= 2LL * shells(R, box[a]) + 1;
+        if (nsh > kMaxShifts) return HSMA_E_ARG;  // sphere too large for the box
     }
 
     hsma_plan_s *pl = new hsma_plan_s();

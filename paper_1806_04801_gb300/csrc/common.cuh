@@ -323,8 +323,9 @@ struct PairArgs {
     int *next_item;
     int *status;
 };
-// variant (FP32 form): targets per thread, 4 (blocks and tiles of 512) or 2
-// (blocks and tiles of 256).
+// variant (FP32 form): one of the codes pair_variant_valid accepts; it fixes
+// the targets per thread -- 4 (blocks and tiles of 512), 3 (384) or 2 (256) --
+// the inner loop (scalar or packed f32x2) and the CTAs per SM.
 int launch_pair(const PairArgs &a, int precision, int variant, int grid, cudaStream_t st);
 bool pair_variant_valid(int variant);
 int pair_targets_per_block(int precision, int variant = 4);

@@ -28,9 +28,9 @@ namespace hsma {
 namespace {
 
 constexpr int kThreads = 128;
-// FP32 form: T targets per thread (T = 4 or 2, by variant); a block of 128 T
-// targets is exactly one in-set tile of 128 T sources, so a particle block's
-// box is its tile's box.
+// FP32 form: T targets per thread (T = 2, 3 or 4, by variant); a block of
+// 128 T targets is exactly one in-set tile of 128 T sources, so a particle
+// block's box is its tile's box.
 constexpr int kT64 = 2;
 constexpr int kTB64 = kThreads * kT64;
 constexpr int kTile64 = 256;
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
     // source-loop unrolling per variant (measured: 4 targets at 4 CTAs/SM
     // prefers 4, at 5 CTAs/SM 8, two targets a full unroll)
     // (packed: 32 pair steps per fold, unrolled fully for two targets and by
-    // half for four)
+    // half for three and four)
     constexpr int UNROLL = X2 ? (T == 2 ? kFold2 / 2 : kFold2 / 4) : (T == 2 ? kFold : (MINB >= 5 ? 8 : 4));
     constexpr int TB = kThreads * T;  // targets per block
     constexpr int TILE = TB;          // sources per tile

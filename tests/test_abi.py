@@ -98,6 +98,9 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
     assert plan(fib_F2=100) == ARG                         # not a Fibonacci number
     assert plan(precision=3) == ARG and plan(precision=-1) == ARG
     assert plan(far_field=2) == ARG
+    # a sphere many box lengths across: more image shifts than a launch grid holds
+    assert plan(box=D3(1e-4, 1.0, 1.0), R=1.0) == ARG      # 20001 x 3 x 3 shifts
+    assert plan(box=D3(1e-12, 1.0, 1.0), R=1.0) == ARG
     assert out.value is None                               # no plan handed out
 
     # update, sharding, tuning and inspection calls without a plan

@@ -192,7 +192,7 @@ int hsma_energy_forces(hsma_plan_t plan, const hsma_particles *x_q, hsma_out *ou
  * potentials: concatenated (offsets[nsys] x 3 / offsets[nsys]) in the same
  * memory space as *all, or NULL.  An error in one system fails the call;
  * status (host array of nsys, or NULL) receives each system's code.
- * Size limits: nsys <= 65535 and, per system, those of hsma_energy_forces;
+ * Size limits: nsys <= 65528 and, per system, those of hsma_energy_forces;
  * beyond them HSMA_E_ARG. */
 int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offsets,
                                const hsma_particles *all, double *energies, double *forces,
@@ -293,7 +293,7 @@ typedef struct hsma_server_s *hsma_server_t;
 
 typedef struct {
     size_t hbm_budget_bytes;  /* device bytes of work in flight; 0 = half the free memory */
-    int max_batch;            /* systems per batched pass (default 64)                    */
+    int max_batch;            /* systems per batched pass, 1..65528 (default 64)          */
     int lanes;                /* concurrent batched passes, 1..16 (default 2)            */
     int precision;            /* hsma_precision of served requests (default 1)           */
 } hsma_server_opts;

@@ -37,9 +37,10 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kInsetBlock = 256;
 // Size limits of the update step.  Systems and image shifts index grid
-// dimensions y / z of several kernels (at most 65535 each); a system's in-set
-// slots, particle indices and work items are 32-bit.
-constexpr int kMaxSystems = 65535;
+// dimensions y / z of several kernels (at most 65535 each; the tensor-core
+// fit pads the system count to a multiple of 8, hence 65528); a system's
+// in-set slots, particle indices and work items are 32-bit.
+constexpr int kMaxSystems = 65528;
 constexpr int kMaxShifts = 65535;
 constexpr long long kMaxInsetSlots = (1LL << 31) - 1;
 

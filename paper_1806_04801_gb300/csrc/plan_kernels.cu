@@ -393,6 +393,16 @@ int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond_ho
     double *scale = nullptr, *vtop = nullptr, *vv = nullptr, *diag = nullptr, *Q1 = nullptr, *Rinv = nullptr,
            *cond = nullptr;
     int *rank_ok = nullptr;
+    // the temporaries are freed on every return path (cudaFree waits for the
+    // device work that uses them)
+    struct Temporaries {
+        void **p[4];
+        ~Temporaries()
+        {
+            for (void **q : p)
+                if (*q) cudaFree(*q);
+        }
+    } temps{{(void **)&scale, (void **)&rank_ok, (void **)&Q1, (void **)&Rinv}};
     size_t nd = (size_t)n;
     HSMA_CUDA_TRY(cudaMalloc(&scale, nd * 4 * sizeof(double) + sizeof(double) + 16));
     vtop = scale + nd;
@@ -427,10 +437,6 @@ int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond_ho
     HSMA_CUDA_TRY(cudaMemcpyAsync(cond_host, cond, sizeof(double), cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaMemcpyAsync(rank_ok_host, rank_ok, sizeof(int), cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(scale);
-    cudaFree(rank_ok);
-    cudaFree(Q1);
-    cudaFree(Rinv);
     return HSMA_OK;
 }
 

@@ -184,7 +184,7 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
     hsma_server_opts o;
     hsma_server_opts_default(&o);
     if (opts) o = *opts;
-    if (o.lanes < 1 || o.lanes > 16 || o.max_batch < 1) return HSMA_E_ARG;
+    if (o.lanes < 1 || o.lanes > 16 || o.max_batch < 1 || o.max_batch > 65528) return HSMA_E_ARG;
     if (o.hbm_budget_bytes == 0) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return HSMA_E_CUDA;

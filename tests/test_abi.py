@@ -154,7 +154,7 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
     assert lib.hsma_server_opts_default(ctypes.byref(so)) == 0
     assert so.max_batch == 64 and so.lanes == 2 and so.precision == hsma.FP32_ACC64
     srv = ctypes.c_void_p()
-    for field, bad in (("lanes", 0), ("lanes", 17), ("max_batch", 0)):
+    for field, bad in (("lanes", 0), ("lanes", 17), ("max_batch", 0), ("max_batch", 65529)):
         o2 = hsma.hsma_server_opts()
         lib.hsma_server_opts_default(ctypes.byref(o2))
         setattr(o2, field, bad)

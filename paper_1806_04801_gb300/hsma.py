@@ -132,13 +132,45 @@ def _is_torch(a):
 
 
 def _ptr_and_dev(a):
+    """(address, on device) of a contiguous float64 torch tensor or numpy
+    array; a CUDA tensor must live on the current device (the library's
+    kernels run there)."""
     if _is_torch(a):
-        if not a.is_contiguous() or a.dtype.itemsize != 8:
+        import torch
+        if not a.is_contiguous() or a.dtype != torch.float64:
             raise ValueError("tensors must be contiguous float64")
+        if a.is_cuda and a.device.index != torch.cuda.current_device():
+            raise ValueError(f"tensor on {a.device}, but the current CUDA device is {torch.cuda.current_device()}")
         return a.data_ptr(), bool(a.is_cuda)
     if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
         raise ValueError("arrays must be C-contiguous float64 numpy arrays")
     return a.ctypes.data, False
+
+
+def _system_arrays(xyz, q, n=None):
+    """Addresses of positions (n, 3) and charges (n,), both host or both
+    device, with n = len(q) unless given; returns (p_xyz, p_q, on_device, n)."""
+    pxyz, dev = _ptr_and_dev(xyz)
+    pq, dev2 = _ptr_and_dev(q)
+    if dev != dev2:
+        raise ValueError("xyz and q must both be host or both device arrays")
+    n = int(q.shape[0]) if n is None else int(n)
+    if tuple(q.shape) != (n,) or tuple(xyz.shape) != (n, 3):
+        raise ValueError(f"expected xyz of shape ({n}, 3) and q of shape ({n},); got {tuple(xyz.shape)} and "
+                         f"{tuple(q.shape)}")
+    return pxyz, pq, dev, n
+
+
+def _offsets(offsets, n=None):
+    """Batch offsets as a contiguous int64 array of nsys + 1 entries, ending
+    at n when n is given (the library itself rejects a first entry other than
+    0 and empty or decreasing systems, with HSMA_E_ARG)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    if off.ndim != 1 or off.shape[0] < 2:
+        raise ValueError("offsets must hold nsys + 1 >= 2 entries")
+    if n is not None and int(off[-1]) != int(n):
+        raise ValueError(f"offsets end at {int(off[-1])}, but the arrays hold {int(n)} particles")
+    return off
 
 
 def _stream_handle(stream):
@@ -258,13 +290,7 @@ class Plan:
         """hsma_energy_forces.  xyz (n, 3) and q (n,) float64, both numpy
         (host) or both torch CUDA tensors (device).  Returns
         (energy, forces or None, potentials or None, n_inset)."""
-        pxyz, dev = _ptr_and_dev(xyz)
-        pq, dev2 = _ptr_and_dev(q)
-        if dev != dev2:
-            raise ValueError("xyz and q must both be host or both device arrays")
-        n = int(q.shape[0])
-        if tuple(xyz.shape) != (n, 3):
-            raise ValueError("xyz must have shape (n, 3)")
+        pxyz, pq, dev, n = _system_arrays(xyz, q)
         f = p = None
         if dev:
             import torch
@@ -288,11 +314,9 @@ class Plan:
         sequence of nsys+1 increasing integers.  Returns (energies, forces,
         potentials, status).  On an error the raised HsmaError carries the
         per-system codes in its ``status``."""
-        pxyz, dev = _ptr_and_dev(xyz)
-        pq, _ = _ptr_and_dev(q)
-        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        off = _offsets(offsets)
         nsys = off.shape[0] - 1
-        n = int(off[-1])
+        pxyz, pq, dev, n = _system_arrays(xyz, q, int(off[-1]))
         f = p = None
         if dev:
             import torch
@@ -317,9 +341,7 @@ class Plan:
 
     # ---------------------------------------------------- target sharding
     def _shard_args(self, xyz, q):
-        pxyz, dev = _ptr_and_dev(xyz)
-        pq, _ = _ptr_and_dev(q)
-        n = int(q.shape[0])
+        pxyz, pq, dev, n = _system_arrays(xyz, q)
         return hsma_particles(n, pxyz, pq, 1 if dev else 0), n
 
     def shard_near(self, xyz, q, part: int, nparts: int):
@@ -341,6 +363,8 @@ class Plan:
         """hsma_shard_far: (index, phi_out, E_out) for this part."""
         part_s, n = self._shard_args(xyz, q)
         mon = np.ascontiguousarray(phi_mon, dtype=np.float64)
+        if mon.shape != (self.info()["n_mon_targets"],):
+            raise ValueError("phi_mon must hold one value per monitoring target")
         idx = np.empty(n, dtype=np.int64)
         phi = np.empty(n)
         fld = np.empty((n, 3))
@@ -362,7 +386,7 @@ class Plan:
 
     def get_tuning(self, offsets) -> dict:
         """hsma_plan_get_tuning: the tuning a call with these offsets would use."""
-        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        off = _offsets(offsets)
         t = hsma_tuning()
         _check(_lib().hsma_plan_get_tuning(self._h, off.shape[0] - 1, off.ctypes.data, ctypes.byref(t)),
                "hsma_plan_get_tuning")
@@ -370,10 +394,8 @@ class Plan:
 
     def autotune(self, xyz, q, offsets=None, cache_path=None) -> dict:
         """hsma_autotune on a batch (offsets None: one system)."""
-        pxyz, dev = _ptr_and_dev(xyz)
-        pq, _ = _ptr_and_dev(q)
-        n = int(q.shape[0])
-        off = np.ascontiguousarray([0, n] if offsets is None else offsets, dtype=np.int64)
+        pxyz, pq, dev, n = _system_arrays(xyz, q)
+        off = _offsets([0, n] if offsets is None else offsets, n)
         part = hsma_particles(n, pxyz, pq, 1 if dev else 0)
         t = hsma_tuning()
         _check(_lib().hsma_autotune(self._h, off.shape[0] - 1, off.ctypes.data, ctypes.byref(part),
@@ -414,6 +436,8 @@ def coulomb_sum(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     pt, dev2 = _ptr_and_dev(tgt)
     if not (dev and dev2):
         raise ValueError("coulomb_sum takes CUDA tensors")
+    if src.dim() != 2 or src.shape[1] != 4 or tgt.dim() != 2 or tgt.shape[1] != 3:
+        raise ValueError("src must have shape (ns, 4) and tgt shape (nt, 3)")
     nt = tgt.shape[0]
     pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
     fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
@@ -434,6 +458,8 @@ def coulomb_sum_static(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     pt, dev2 = _ptr_and_dev(tgt)
     if not (dev and dev2):
         raise ValueError("coulomb_sum_static takes CUDA tensors")
+    if src.dim() != 2 or src.shape[1] != 4 or tgt.dim() != 2 or tgt.shape[1] != 3:
+        raise ValueError("src must have shape (ns, 4) and tgt shape (nt, 3)")
     nt = tgt.shape[0]
     pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
     fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
@@ -451,6 +477,8 @@ def basis(pts, p: int, Rs: float, stream=None):
     pp, dev = _ptr_and_dev(pts)
     if not dev:
         raise ValueError("basis takes a CUDA tensor")
+    if pts.dim() != 2 or pts.shape[1] != 3:
+        raise ValueError("pts must have shape (np, 3)")
     out = torch.empty((pts.shape[0], (p + 1) ** 2), dtype=torch.float64, device=pts.device)
     _check(_lib().hsma_basis(int(p), float(Rs), pts.shape[0], pp, out.data_ptr(), _stream_handle(stream)),
            "hsma_basis")
@@ -507,24 +535,36 @@ class Server:
         _check(L.hsma_server_create(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon),
                                     ctypes.byref(o)), "hsma_server_create")
         self._h = h
+        self._sizes = {}  # ticket -> particles, so result() sizes the force buffer itself
 
     def submit(self, xyz: np.ndarray, q: np.ndarray) -> int:
         """hsma_server_submit: queue one configuration (host arrays); returns its ticket."""
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         q = np.ascontiguousarray(q, dtype=np.float64)
+        if q.ndim != 1 or xyz.shape != (q.shape[0], 3):
+            raise ValueError(f"expected xyz of shape ({q.shape[0]}, 3) and q of shape (n,)")
         t = ctypes.c_int64()
         _check(_lib().hsma_server_submit(self._h, q.shape[0], xyz.ctypes.data, q.ctypes.data, ctypes.byref(t)),
                "hsma_server_submit")
+        self._sizes[int(t.value)] = int(q.shape[0])
         return int(t.value)
 
     def result(self, ticket: int, n: int | None = None, wait: bool = True, forces: bool = True):
         """(code, energy, forces or None, info dict); code HSMA_E_AGAIN (-10)
-        when not ready and wait is False."""
+        when not ready and wait is False.  The force buffer is sized from the
+        submitted request (n, if given, must agree with it)."""
+        ticket = int(ticket)
+        n_sub = self._sizes.get(ticket)
+        if n is not None and n_sub is not None and int(n) != n_sub:
+            raise ValueError(f"ticket {ticket} holds {n_sub} particles, not {n}")
+        n = n_sub if n_sub is not None else n
         e = ctypes.c_double()
         info = hsma_request_info()
         f = np.empty((n, 3)) if (forces and n) else None
-        code = _lib().hsma_server_result(self._h, int(ticket), 1 if wait else 0, ctypes.byref(e),
+        code = _lib().hsma_server_result(self._h, ticket, 1 if wait else 0, ctypes.byref(e),
                                          f.ctypes.data if f is not None else None, ctypes.byref(info))
+        if code != -10:  # collected (or unknown): the ticket is gone
+            self._sizes.pop(ticket, None)
         return code, e.value, f, {k: getattr(info, k) for k, _ in hsma_request_info._fields_}
 
     def cancel(self, ticket: int) -> int:

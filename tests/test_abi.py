@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -173,3 +175,39 @@ def test_every_error_code_has_its_own_message(lib):
     assert all(m != "unknown error" for m in msgs)
     assert hsma.strerror(-13) == "unknown error" and hsma.strerror(7) == "unknown error"
     assert "static scratch" in hsma.strerror(-11) and "memory budget" in hsma.strerror(-11)
+
+
+def test_binding_checks_shapes_before_calling_the_library(lib):
+    """The Python binding passes sizes to the C ABI that it derives from the
+    arrays, so it checks them first: a mismatch raises ValueError before any
+    library call (here on a plan object that holds no library handle)."""
+    import torch
+    from paper_1806_04801_gb300 import hsma
+    plan = hsma.Plan.__new__(hsma.Plan)
+    plan._h = None
+    x5, q5 = np.zeros((5, 3)), np.zeros(5)
+    with pytest.raises(ValueError, match="shape"):
+        plan.energy_forces(np.zeros((4, 3)), q5)
+    with pytest.raises(ValueError, match="shape"):
+        plan.energy_forces(np.zeros((5, 2)), q5)
+    with pytest.raises(ValueError, match="float64"):
+        plan.energy_forces(x5.astype(np.float32), q5)
+    with pytest.raises(ValueError, match="float64"):
+        plan.energy_forces(torch.zeros((5, 3), dtype=torch.int64), torch.zeros(5, dtype=torch.int64))
+    with pytest.raises(ValueError, match="contiguous"):
+        plan.energy_forces(np.zeros((3, 5)).T, q5)
+    # batched: the offsets must end where the arrays end
+    with pytest.raises(ValueError, match=r"shape \(7, 3\)"):
+        plan.energy_forces_batched(x5, q5, [0, 2, 7])
+    with pytest.raises(ValueError, match="shape"):
+        plan.energy_forces_batched(x5, np.zeros(4), [0, 2, 5])
+    with pytest.raises(ValueError, match="entries"):
+        plan.energy_forces_batched(x5, q5, [5])
+    with pytest.raises(ValueError, match="offsets end at 4"):
+        plan.autotune(x5, q5, [0, 4])
+    with pytest.raises(ValueError, match="shape"):
+        plan.shard_near(np.zeros((6, 3)), q5, 0, 2)
+    # direct sums and the basis take (ns, 4) sources, (nt, 3) targets and points
+    with pytest.raises(ValueError):
+        hsma.coulomb_sum(np.zeros((4, 4)), np.zeros((2, 3)))        # host arrays
+    del plan

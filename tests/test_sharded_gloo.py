@@ -3,7 +3,8 @@
 Two gloo processes run paper_1806_04801_gb300.sharded.shard_update with a
 compute backend built from the FP64 oracle (the test stands it in for the
 CUDA library, which needs a GPU); their exchanges are real torch.distributed
-all-reduces.  The sharded energy and forces must equal the unsharded oracle's.
+all-reduces.  The sharded energy and forces must equal the unsharded oracle's, and a rank
+that fails before the exchange must end the others' step with an error.
 """
 import os
 import socket
@@ -115,3 +116,62 @@ def test_local_driver_with_oracle_backend_any_part_count():
         U, F, pot = sharded.shard_update_local(OracleBackend(WORKLOAD), xyz, q, nparts)
         assert abs(U - ref["energy"]) <= 1e-12 * abs(ref["energy"])
         np.testing.assert_allclose(F, ref["forces"], rtol=0, atol=1e-12 * np.abs(ref["forces"]).max())
+
+
+class _DyingBackend:
+    """Stands in for a rank whose near-field stage fails (a host-side
+    fault: the exception a failed device call would raise)."""
+
+    def near(self, xyz, q, part, nparts):
+        raise RuntimeError("injected failure in the near-field stage")
+
+    def far(self, xyz, q, phi_mon, part, nparts):
+        raise AssertionError("not reached")
+
+
+def _worker_one_rank_fails(rank, world, port, out_dir):
+    import time
+    from datetime import timedelta
+    import torch.distributed as dist
+    from paper_1806_04801_gb300 import sharded
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=timedelta(seconds=10))
+    xyz, q = I.uniform_pm1(200, WORKLOAD.box, seed_offset=404)
+    backend = OracleBackend(WORKLOAD) if rank == 0 else _DyingBackend()
+    t0 = time.time()
+    try:
+        sharded.shard_update(backend, xyz, q, sharded.TorchComm())
+        outcome = "completed"
+    except Exception as e:  # recorded for the parent, which checks it
+        outcome = f"{type(e).__name__}: {e}".replace("\n", " ")[:300]
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(f"{time.time() - t0:.3f}\n{outcome}\n")
+
+
+def test_a_failing_rank_ends_the_sharded_step_with_an_error_on_the_others():
+    """Rank 1 fails before the exchange of the monitoring potentials and
+    leaves; rank 0's all-reduce then ends with an error (the peer's closed
+    connection, at the latest the process group's 10 s timeout) instead of
+    waiting for ever.  Host-side failure only: no device is involved."""
+    import multiprocessing as mpl
+    ctx = mpl.get_context("spawn")
+    with tempfile.TemporaryDirectory() as d:
+        port = _free_port()
+        procs = [ctx.Process(target=_worker_one_rank_fails, args=(r, 2, port, d)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+        alive = [p for p in procs if p.is_alive()]
+        for p in alive:  # only the processes this test started
+            p.terminate()
+            p.join(timeout=10)
+        assert not alive, "a rank was still running after 120 s"
+        res = {}
+        for r in range(2):
+            with open(os.path.join(d, f"r{r}.txt")) as f:
+                t, outcome = f.read().splitlines()[:2]
+            res[r] = (float(t), outcome)
+    assert "injected failure" in res[1][1]
+    assert res[0][1] != "completed", res[0]
+    assert res[0][0] < 60.0, res[0]

@@ -137,6 +137,16 @@ typedef struct {
 
 int hsma_plan_get_info(hsma_plan_t plan, hsma_plan_info_t *info);
 
+/* The dimensions hsma_plan would give a plan with these arguments, computed
+ * on the host alone (no device, no allocation): N_b = (p+1)^2 and the fitted
+ * columns (Sec. II.A), monitoring targets, F2, F1 and N_o = 6(F2+1) of the
+ * Fibonacci integration (Sec. II.B), the image shifts tested for the in-set,
+ * R0, alpha = Rs/R0 and Delta r (Eq. "cd").  cond_estimate is 0 (it needs
+ * the QR).  Argument checks and errors as hsma_plan's host-side ones
+ * (HSMA_E_ARG); for sizing plans before any device exists. */
+int hsma_plan_dims(const double box[3], int bc, int p, double R, int Q, int Kmon, const hsma_opts *opts,
+                   hsma_plan_info_t *info);
+
 /* Change the stream a plan works on (NULL = legacy default stream). */
 int hsma_plan_set_stream(hsma_plan_t plan, void *stream);
 

@@ -924,6 +924,58 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
 
 std::mutex g_scratch_mu;
 
+// Everything a plan's parameters fix before any device work: the checked
+// options and the derived sizes (basis, fitted columns, monitoring targets,
+// Fibonacci rule, image shells, Delta r).  Pure host arithmetic; shared by
+// hsma_plan and hsma_plan_dims.
+struct PlanParams {
+    hsma_opts o;
+    double R0, dr;
+    int Nb, ncols, nmon, F2, F1, Ks[3], nshifts;
+};
+
+int plan_params(const double box[3], int bc, int p, double R, int Q, int Kmon, const hsma_opts *opts,
+                PlanParams *pp)
+{
+    hsma_opts o;
+    hsma_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0)) return HSMA_E_ARG;
+    if (bc != HSMA_BC_PERIODIC && bc != HSMA_BC_GROUNDED) return HSMA_E_ARG;
+    if (p < 1 || p > 40) return HSMA_E_ARG;
+    if (o.precision < 0 || o.precision > 2) return HSMA_E_ARG;
+    if (o.far_field != 0 && o.far_field != 1) return HSMA_E_ARG;
+    const double R0 = 0.5 * sqrt(box[0] * box[0] + box[1] * box[1] + box[2] * box[2]);
+    if (!(R > R0) || !isfinite(R)) return HSMA_E_ARG;
+    const int Nb = (p + 1) * (p + 1);
+    const int ncols = (bc == HSMA_BC_PERIODIC) ? Nb - 1 : Nb;
+    if (Kmon < ncols || Kmon > 16384) return HSMA_E_ARG;
+    int F2 = 0, F1 = 0;
+    if (o.fib_F2 > 0) {
+        F2 = o.fib_F2;
+        if (!fib_pred(F2, &F1) || F2 < 2) return HSMA_E_ARG;
+    } else {
+        if (Q < 12) return HSMA_E_ARG;
+        fib_from_q(Q, &F2, &F1);
+    }
+    long long nsh = 1;
+    for (int a = 0; a < 3; ++a) {
+        pp->Ks[a] = shells(R, box[a]);
+        nsh *= 2LL * pp->Ks[a] + 1;
+    }
+    if (nsh > kMaxShifts) return HSMA_E_ARG;  // sphere too large for the box
+    pp->o = o;
+    pp->R0 = R0;
+    pp->dr = (o.dr_rel > 0 ? o.dr_rel : (bc == HSMA_BC_PERIODIC ? 1e-5 : 1e-4)) * R;
+    pp->Nb = Nb;
+    pp->ncols = ncols;
+    pp->nmon = (bc == HSMA_BC_PERIODIC) ? 2 * Kmon : Kmon;
+    pp->F2 = F2;
+    pp->F1 = F1;
+    pp->nshifts = (int)nsh;
+    return HSMA_OK;
+}
+
 }  // namespace
 
 void hsma::plan_trim_workspace(hsma_plan_t p, size_t max_keep)
@@ -987,32 +1039,11 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
 {
     if (!out || !box) return HSMA_E_ARG;
     *out = nullptr;
-    hsma_opts o;
-    hsma_opts_default(&o);
-    if (opts) o = *opts;
-    if (!(box[0] > 0 && box[1] > 0 && box[2] > 0)) return HSMA_E_ARG;
-    if (bc != HSMA_BC_PERIODIC && bc != HSMA_BC_GROUNDED) return HSMA_E_ARG;
-    if (p < 1 || p > 40) return HSMA_E_ARG;
-    if (o.precision < 0 || o.precision > 2) return HSMA_E_ARG;
-    const double R0 = 0.5 * sqrt(box[0] * box[0] + box[1] * box[1] + box[2] * box[2]);
-    if (!(R > R0) || !isfinite(R)) return HSMA_E_ARG;
-    const int Nb = (p + 1) * (p + 1);
-    const int ncols = (bc == HSMA_BC_PERIODIC) ? Nb - 1 : Nb;
-    if (Kmon < ncols || Kmon > 16384) return HSMA_E_ARG;
-    int F2 = 0, F1 = 0;
-    if (o.fib_F2 > 0) {
-        F2 = o.fib_F2;
-        if (!fib_pred(F2, &F1) || F2 < 2) return HSMA_E_ARG;
-    } else {
-        if (Q < 12) return HSMA_E_ARG;
-        fib_from_q(Q, &F2, &F1);
-    }
-
-    {
-        long long nsh = 1;
-        for (int a = 0; a < 3; ++a) nsh *= 2LL * shells(R, box[a]) + 1;
-        if (nsh > kMaxShifts) return HSMA_E_ARG;  // sphere too large for the box
-    }
+    PlanParams pp;
+    if (int e = plan_params(box, bc, p, R, Q, Kmon, opts, &pp)) return e;
+    const hsma_opts &o = pp.o;
+    const double R0 = pp.R0;
+    const int Nb = pp.Nb, ncols = pp.ncols, F2 = pp.F2, F1 = pp.F1;
 
     hsma_plan_s *pl = new hsma_plan_s();
     for (int a = 0; a < 3; ++a) pl->L[a] = box[a];
@@ -1022,23 +1053,18 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     pl->ncols = ncols;
     pl->K = Kmon;
     pl->mon_faces = (bc == HSMA_BC_GROUNDED) ? 1 : 0;
-    pl->nmon = (bc == HSMA_BC_PERIODIC) ? 2 * Kmon : Kmon;
+    pl->nmon = pp.nmon;
     pl->F2 = F2;
     pl->F1 = F1;
     pl->ndir = 2 * (F2 + 1);
     pl->Rs = R;
     pl->R0 = R0;
     pl->alpha = R / R0;
-    double dr_rel = o.dr_rel > 0 ? o.dr_rel : (bc == HSMA_BC_PERIODIC ? 1e-5 : 1e-4);
-    pl->dr = dr_rel * R;
+    pl->dr = pp.dr;
     pl->precision = o.precision;
     pl->use_graphs = o.use_graphs;
     pl->profile = o.profile;
     pl->stream = (cudaStream_t)o.stream;
-    if (o.far_field != 0 && o.far_field != 1) {
-        delete pl;
-        return HSMA_E_ARG;
-    }
     pl->far_field = o.far_field;
     {
         const char *e = getenv("HSMA_TEST_STALL_WAIT");
@@ -1065,8 +1091,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     snprintf(pl->device_name, sizeof(pl->device_name), "%s", prop.name);
 
     // image shift table: k = 0 first, then lexicographic (kx, ky, kz)
-    int Ks[3];
-    for (int a = 0; a < 3; ++a) Ks[a] = shells(R, box[a]);
+    const int *Ks = pp.Ks;
     std::vector<int4> sh;
     sh.push_back(make_int4(0, 0, 0, 0));
     for (int kx = -Ks[0]; kx <= Ks[0]; ++kx)
@@ -1222,6 +1247,31 @@ int hsma_plan_get_info(hsma_plan_t pl, hsma_plan_info_t *info)
     info->dr = pl->dr;
     info->cond_estimate = pl->cond;
     info->precision = pl->precision;
+    return HSMA_OK;
+}
+
+int hsma_plan_dims(const double box[3], int bc, int p, double R, int Q, int Kmon, const hsma_opts *opts,
+                   hsma_plan_info_t *info)
+{
+    if (!box || !info) return HSMA_E_ARG;
+    PlanParams pp;
+    if (int e = plan_params(box, bc, p, R, Q, Kmon, opts, &pp)) return e;
+    info->bc = bc;
+    info->p = p;
+    info->n_basis = pp.Nb;
+    info->n_cols = pp.ncols;
+    info->Kmon = Kmon;
+    info->n_mon_targets = pp.nmon;
+    info->F2 = pp.F2;
+    info->F1 = pp.F1;
+    info->n_images = 6 * (pp.F2 + 1);
+    info->n_shifts = pp.nshifts;
+    info->Rs = R;
+    info->R0 = pp.R0;
+    info->alpha = R / pp.R0;
+    info->dr = pp.dr;
+    info->cond_estimate = 0.0;
+    info->precision = pp.o.precision;
     return HSMA_OK;
 }
 

@@ -73,6 +73,8 @@ SIGNATURES = {
     "hsma_plan": (_I, [ctypes.POINTER(_VP), ctypes.POINTER(_D), _I, _I, _D, _I, _I, ctypes.POINTER(hsma_opts)]),
     "hsma_plan_destroy": (None, [_VP]),
     "hsma_plan_get_info": (_I, [_VP, ctypes.POINTER(hsma_plan_info_t)]),
+    "hsma_plan_dims": (_I, [ctypes.POINTER(_D), _I, _I, _D, _I, _I, ctypes.POINTER(hsma_opts),
+                            ctypes.POINTER(hsma_plan_info_t)]),
     "hsma_plan_set_stream": (_I, [_VP, _VP]),
     "hsma_plan_set_precision": (_I, [_VP, _I]),
     "hsma_plan_footprint": (_I, [_VP, _I64, ctypes.POINTER(ctypes.c_size_t)]),
@@ -194,6 +196,22 @@ def fp32_peak() -> tuple:
     if rc != 0:
         raise HsmaError(rc, "hsma_fp32_peak")
     return sc.value, pk.value
+
+
+def plan_dims(box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64, dr_rel: float = 0.0,
+              fib_F2: int = 0) -> dict:
+    """hsma_plan_dims: the sizes a plan with these arguments would have (the
+    fields of Plan.info() but cond_estimate), on the host, without a device."""
+    o = hsma_opts()
+    _check(_lib().hsma_opts_default(ctypes.byref(o)), "hsma_opts_default")
+    o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    o.dr_rel = float(dr_rel)
+    o.fib_F2 = int(fib_F2)
+    box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
+    i = hsma_plan_info_t()
+    _check(_lib().hsma_plan_dims(box_arr, int(bc), int(p), float(R), int(Q), int(Kmon), ctypes.byref(o),
+                                 ctypes.byref(i)), "hsma_plan_dims")
+    return {k: getattr(i, k) for k, _ in hsma_plan_info_t._fields_}
 
 
 def version() -> str:

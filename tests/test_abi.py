@@ -211,3 +211,49 @@ def test_binding_checks_shapes_before_calling_the_library(lib):
     with pytest.raises(ValueError):
         hsma.coulomb_sum(np.zeros((4, 4)), np.zeros((2, 3)))        # host arrays
     del plan
+
+
+def test_plan_dims_follow_the_readings_of_the_paper(lib):
+    """hsma_plan_dims (host only) against the oracle's own, independently
+    written rules: F2 from Q (the Fibonacci number whose N_o = 6(F2 + 1) is
+    nearest to Q, ties to the larger; Sec. II.B), the image shells per axis
+    (the smallest K with (K + 1/2) L_a >= Rs; Sec. II.A), the fitted columns
+    and monitoring targets (periodic: n = 0 column dropped, points paired with
+    their wrapped partners; Sec. II.A), and Delta r (Sec. III)."""
+    import math
+    import oracle
+    from oracle import hsma as oh
+    from paper_1806_04801_gb300 import hsma
+    unit = (1.0, 1.0, 1.0)
+    for Q in list(range(12, 400)) + [1000, 2000, 2268, 3600, 5928, 6000, 8000, 9588, 20000, 123456]:
+        d = hsma.plan_dims(unit, hsma.PERIODIC, 8, 1.5, Q, 600)
+        F2, F1 = oh.fib_from_points(Q)
+        assert (d["F2"], d["F1"], d["n_images"]) == (F2, F1, 6 * (F2 + 1)), Q
+    # the workloads' surface-point counts (reading of Q) and the paper's N_o = 5928
+    assert [hsma.plan_dims(unit, 0, 8, 1.5, Q, 600)["F2"] for Q in (2000, 8000, 6000)] == [377, 1597, 987]
+    assert hsma.plan_dims(unit, 0, 8, 1.5, 0, 600, fib_F2=987)["n_images"] == 5928
+    with pytest.raises(hsma.HsmaError):
+        hsma.plan_dims(unit, 0, 8, 1.5, 0, 600, fib_F2=988)
+    for box, R in ((unit, 1.5), (unit, 2.0 * 0.5 * math.sqrt(3.0)), ((1.0, 1.3, 0.8), None), ((1.0, 1.0, 2.0), None),
+                   ((2.0, 2.0, 2.0), 2.0 * math.sqrt(3.0)), (unit, 10.0)):
+        R0 = 0.5 * math.sqrt(sum(b * b for b in box))
+        R = math.sqrt(3.0) * R0 if R is None else R
+        for bc in (hsma.PERIODIC, hsma.GROUNDED):
+            d = hsma.plan_dims(box, bc, 10, R, 6000, 1500)
+            shifts = 1
+            for La in box:
+                shifts *= 2 * oracle.num_shells(R, La) + 1
+            assert d["n_shifts"] == shifts, (box, R)
+            assert d["n_basis"] == 121 and d["n_cols"] == (120 if bc == hsma.PERIODIC else 121)
+            assert d["n_mon_targets"] == (3000 if bc == hsma.PERIODIC else 1500) and d["Kmon"] == 1500
+            assert d["dr"] == pytest.approx((1e-5 if bc == hsma.PERIODIC else 1e-4) * R, rel=1e-15)
+            assert d["R0"] == pytest.approx(R0, rel=1e-15) and d["alpha"] == pytest.approx(R / R0, rel=1e-15)
+            assert d["cond_estimate"] == 0.0
+    assert hsma.plan_dims(unit, 0, 8, 1.5, 2000, 600)["n_shifts"] == 27      # 3 x 3 x 3 copies at Rs = 1.5 L
+    assert hsma.plan_dims(unit, 0, 8, 1.5, 2000, 600, dr_rel=3e-6)["dr"] == pytest.approx(4.5e-6, rel=1e-15)
+    assert hsma.plan_dims(unit, 0, 8, 1.5, 2000, 600, precision="fp32_tc")["precision"] == hsma.FP32_TC_FIT
+    # the same argument checks as hsma_plan
+    for args in (((1.0, 0.0, 1.0), 0, 8, 1.5, 2000, 600), (unit, 2, 8, 1.5, 2000, 600), (unit, 0, 41, 1.5, 2000, 600),
+                 (unit, 0, 8, 0.8, 2000, 600), (unit, 0, 8, 1.5, 2000, 79), (unit, 0, 8, 1.5, 11, 600)):
+        with pytest.raises(hsma.HsmaError):
+            hsma.plan_dims(*args)

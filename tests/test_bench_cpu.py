@@ -30,3 +30,38 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert r["impl"] == "reference" and r["value"] > 0 and r["unit"] == "systems/s"
     assert r["cpu_baseline"]["kind"] == "oracle" and r["e2e"]["h2d_bytes_per_step"] == 0
     assert r["config"]["N"] == 100_000
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path):
+    """bench.py's clock record: median SM clock under load, the maximum, and
+    the throttle reasons seen, parsed from nvidia-smi's noheader/nounits CSV
+    rows (as sampled during the timed region)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Done:  # stands in for the finished nvidia-smi process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    rows = [
+        "0, 2070, 2070, 812.40, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.02, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1201.75, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler()
+    cs.path, cs.proc = str(path), _Done()
+    r = cs.stop()
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0 and r["samples"] == 3
+    assert r["power_w_max"] == 1390.02
+    assert r["reasons"] == ["sw_power_cap"]
+    assert not path.exists()  # the temporary record is removed
+    path.write_text("0, 1400, 2070, 700.0, 0x0000000000000040, Not Active, Active, Not Active, Not Active\n")
+    cs.path, cs.proc = str(path), _Done()
+    assert cs.stop()["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler().stop()["reasons"] == ["nvidia-smi unavailable"]

@@ -175,6 +175,15 @@ def _offsets(offsets, n=None):
     return off
 
 
+def _precision_code(precision) -> int:
+    """hsma_precision code of a name ("fp64", "fp32", "fp32_tc") or a code."""
+    if isinstance(precision, str):
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}, not {precision!r}")
+        return PRECISIONS[precision]
+    return int(precision)
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -204,7 +213,7 @@ def plan_dims(box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_
     fields of Plan.info() but cond_estimate), on the host, without a device."""
     o = hsma_opts()
     _check(_lib().hsma_opts_default(ctypes.byref(o)), "hsma_opts_default")
-    o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    o.precision = _precision_code(precision)
     o.dr_rel = float(dr_rel)
     o.fib_F2 = int(fib_F2)
     box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
@@ -233,7 +242,7 @@ class Plan:
         L = _lib()
         o = hsma_opts()
         _check(L.hsma_opts_default(ctypes.byref(o)), "hsma_opts_default")
-        o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+        o.precision = _precision_code(precision)
         o.dr_rel = float(dr_rel)
         o.fib_F2 = int(fib_F2)
         o.stream = _stream_handle(stream)
@@ -267,9 +276,7 @@ class Plan:
 
     def set_precision(self, precision):
         """hsma_plan_set_precision: "fp64", "fp32" or "fp32_tc" for later calls."""
-        if isinstance(precision, str):
-            precision = PRECISIONS[precision]
-        _check(_lib().hsma_plan_set_precision(self._h, int(precision)), "hsma_plan_set_precision")
+        _check(_lib().hsma_plan_set_precision(self._h, _precision_code(precision)), "hsma_plan_set_precision")
 
     def footprint(self, n: int) -> int:
         """hsma_plan_footprint: device bytes one call with n particles needs."""
@@ -459,8 +466,7 @@ def coulomb_sum(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     nt = tgt.shape[0]
     pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
     fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
-    if isinstance(precision, str):
-        precision = PRECISIONS[precision]
+    precision = _precision_code(precision)
     _check(_lib().hsma_coulomb_sum(src.shape[0], ps, nt, pt, pot.data_ptr(),
                                    fld.data_ptr() if fld is not None else None, int(precision),
                                    _stream_handle(stream)), "hsma_coulomb_sum")
@@ -481,8 +487,7 @@ def coulomb_sum_static(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     nt = tgt.shape[0]
     pot = torch.empty(nt, dtype=torch.float64, device=tgt.device)
     fld = torch.empty((nt, 3), dtype=torch.float64, device=tgt.device) if field else None
-    if isinstance(precision, str):
-        precision = PRECISIONS[precision]
+    precision = _precision_code(precision)
     _check(_lib().hsma_coulomb_sum_static(src.shape[0], ps, nt, pt, pot.data_ptr(),
                                           fld.data_ptr() if fld is not None else None, int(precision),
                                           _stream_handle(stream)), "hsma_coulomb_sum_static")
@@ -544,7 +549,7 @@ class Server:
         L = _lib()
         o = hsma_server_opts()
         _check(L.hsma_server_opts_default(ctypes.byref(o)), "hsma_server_opts_default")
-        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.precision = _precision_code(precision)
         o.lanes = int(lanes)
         o.max_batch = int(max_batch)
         o.hbm_budget_bytes = int(hbm_budget_bytes)

@@ -257,3 +257,11 @@ def test_plan_dims_follow_the_readings_of_the_paper(lib):
                  (unit, 0, 8, 0.8, 2000, 600), (unit, 0, 8, 1.5, 2000, 79), (unit, 0, 8, 1.5, 11, 600)):
         with pytest.raises(hsma.HsmaError):
             hsma.plan_dims(*args)
+
+
+def test_binding_precision_names(lib):
+    from paper_1806_04801_gb300 import hsma
+    assert hsma.plan_dims((1.0, 1.0, 1.0), 0, 8, 1.5, 2000, 600, precision="fp64")["precision"] == hsma.FP64
+    assert hsma.plan_dims((1.0, 1.0, 1.0), 0, 8, 1.5, 2000, 600, precision=2)["precision"] == hsma.FP32_TC_FIT
+    with pytest.raises(ValueError, match="precision must be one of"):
+        hsma.plan_dims((1.0, 1.0, 1.0), 0, 8, 1.5, 2000, 600, precision="fp16")

@@ -265,3 +265,47 @@ def test_binding_precision_names(lib):
     assert hsma.plan_dims((1.0, 1.0, 1.0), 0, 8, 1.5, 2000, 600, precision=2)["precision"] == hsma.FP32_TC_FIT
     with pytest.raises(ValueError, match="precision must be one of"):
         hsma.plan_dims((1.0, 1.0, 1.0), 0, 8, 1.5, 2000, 600, precision="fp16")
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "hsma.h"
+int main(void)
+{
+    hsma_opts o;
+    double box[3] = {1.0, 1.0, 1.0};
+    hsma_plan_info_t info;
+    if (hsma_opts_default(&o) != HSMA_OK) return 1;
+    if (hsma_plan_dims(box, HSMA_BC_PERIODIC, 12, 1.5, 8000, 2000, &o, &info) != HSMA_OK) return 2;
+    if (hsma_plan(NULL, box, HSMA_BC_PERIODIC, 12, 1.5, 8000, 2000, &o) != HSMA_E_ARG) return 3;
+    printf("%s|%d|%d|%d|%d|%s\n", hsma_version(), info.F2, info.n_images, info.n_shifts, info.n_cols,
+           hsma_strerror(HSMA_E_NONNEUTRAL));
+    return 0;
+}
+"""
+
+
+@pytest.mark.parametrize("lang", ["c99", "c++17"])
+def test_header_serves_plain_c_and_cpp_clients(lib, tmp_path, lang):
+    """include/hsma.h compiles as pedantic C99 and as C++17 without warnings,
+    and a client built from it links against libhsma.so and calls the
+    host-only entry points (no device needed)."""
+    import shutil
+    import subprocess
+    from paper_1806_04801_gb300 import hsma
+    cc = shutil.which("gcc" if lang == "c99" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("client.c" if lang == "c99" else "client.cpp")
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(hsma.LIB_PATH)
+    r = subprocess.run([cc, f"-std={lang}", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lhsma",
+                        f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    version, F2, n_images, n_shifts, n_cols, msg = out.stdout.strip().split("|")
+    assert "sm_103a" in version and (F2, n_images, n_shifts, n_cols) == ("1597", "9588", "27", "168")
+    assert msg == "periodic system is not charge neutral"

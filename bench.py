@@ -645,35 +645,50 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_step = float(t.item())
 
+    def side(fn):
+        """A secondary figure: its result, or the error it raised (the
+        headline figures above do not depend on it and are printed anyway)."""
+        try:
+            return fn()
+        except Exception as e:  # reported in the JSON line, not swallowed
+            return {"error": f"{type(e).__name__}: {e}"[:500]}
+
     accuracy = None
     if not args.no_check and rank == 0:
-        with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as p64:
-            U64, F64, _, _ = p64.energy_forces(dx, dq)
-        Uc, Fc, _, _ = plan.energy_forces(dx, dq)
-        dF = (Fc - F64).double()
-        accuracy = {"reference": "FP64 GPU path (same inputs)",
+        def check():
+            with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp64") as p64:
+                U64, F64, _, _ = p64.energy_forces(dx, dq)
+            Uc, Fc, _, _ = plan.energy_forces(dx, dq)
+            dF = (Fc - F64).double()
+            return {"reference": "FP64 GPU path (same inputs)",
                     "rel_energy_err": abs(Uc - U64) / abs(U64),
                     "rms_force_err_rel": float(dF.pow(2).mean().sqrt() / F64.pow(2).mean().sqrt()),
                     "energy": Uc, "energy_fp64": U64}
+        accuracy = side(check)
 
     extras = None
     if rank == 0 and world == 1 and not args.no_extras:
         wb = I.BATCH_PERIODIC
-        with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=args.precision) as pb32, \
-                hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
-            extras = {"batched": run_batched(pb32, pb64, max(3, min(args.steps, 5)), 2, flush)}
-        extras["serving"] = run_serving(args.requests)
-        extras["paper_config"] = run_paper_config(max(3, min(args.steps, 5)), 2, args.precision)
-        extras["series_far_field"] = run_series_far_field(dx, dq, w, args.precision, tuning, phases[5],
-                                                          float(plan.energy_forces(dx, dq)[0]))
+
+        def batched():
+            with hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision=args.precision) as pb32, \
+                    hsma.Plan(wb.box, wb.bc, wb.p, wb.R, wb.Q, wb.Kmon, precision="fp64") as pb64:
+                return run_batched(pb32, pb64, max(3, min(args.steps, 5)), 2, flush)
+        extras = {"batched": side(batched)}
+        extras["serving"] = side(lambda: run_serving(args.requests))
+        extras["paper_config"] = side(lambda: run_paper_config(max(3, min(args.steps, 5)), 2, args.precision))
+        extras["series_far_field"] = side(lambda: run_series_far_field(
+            dx, dq, w, args.precision, tuning, phases[5], float(plan.energy_forces(dx, dq)[0])))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is an N = 1 figure
-        r = cpu_oracle_rate(xyz, q, w)
-        cpu = {"value": r["systems_per_s"], "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
-               "sample": (f"full monitoring-point sums and fit, near-field particle sums on "
-                          f"{r['particles_sampled']} of {n} particles, extrapolated linearly in N"),
-               "pairs_per_s": r["pairs_per_s"]}
+        def cpu_baseline():
+            r = cpu_oracle_rate(xyz, q, w)
+            return {"value": r["systems_per_s"], "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
+                    "sample": (f"full monitoring-point sums and fit, near-field particle sums on "
+                               f"{r['particles_sampled']} of {n} particles, extrapolated linearly in N"),
+                    "pairs_per_s": r["pairs_per_s"]}
+        cpu = side(cpu_baseline)
 
     if rank != 0:
         if dist:

@@ -65,3 +65,27 @@ def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path):
     cs.path, cs.proc = str(path), _Done()
     assert cs.stop()["reasons"] == ["hw_thermal_slowdown"]
     assert bench.ClockSampler().stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_profile_commands_parse_with_the_current_bench(monkeypatch):
+    """Every bench.py command quoted in profiles/ (the commands the ncu
+    summaries were made with) still parses with bench.py's options, and
+    names only files that are in the repository."""
+    import glob
+    import re
+    import shlex
+    sys.path.insert(0, ROOT)
+    import bench
+    cmds = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"python (bench\.py[^\n]*)", text):
+            cmds.append((os.path.basename(path), shlex.split(m.group(1))))
+    assert len(cmds) >= 6
+    for name, argv in cmds:
+        assert os.path.exists(os.path.join(ROOT, argv[0])), (name, argv[0])
+        monkeypatch.setattr(sys, "argv", argv)
+        args = bench.parse()  # exits (SystemExit) on an unknown option
+        if args.tuning:
+            v, i = bench.fixed_tuning(args)
+            assert v in (2, 4, 5, 12, 13, 14, 15, 16, 17) and i >= 1, (name, args.tuning)

@@ -12,7 +12,7 @@ import threading
 import numpy as np
 import pytest
 
-from gpu_common import TOL, assert_within, energy_floor, errors, rel_energy_err, rms, to_dev
+from gpu_common import TOL, energy_floor, errors, rel_energy_err, rms, to_dev
 from paper_1806_04801_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu

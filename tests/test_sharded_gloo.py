@@ -11,7 +11,6 @@ import socket
 import tempfile
 
 import numpy as np
-import pytest
 
 from paper_1806_04801_gb300 import inputs as I
 

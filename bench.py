@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--precision", default="fp32_tc", choices=["fp32", "fp64", "fp32_tc"],
                     help="fp32_tc (default): FP32 pair sums with double-float accumulation, split-BF16 "
                          "tensor-core fit + one refinement; fp32: the same with an FP64 fit; fp64: parity form")
-    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--n", "--particles", dest="n", type=int, default=100_000,
+                    help="particles of the periodic workload (--particles under torchrun, where --n is ambiguous)")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy check")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
@@ -237,6 +238,7 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
         e1.record()
         e1.synchronize()
         return U, e0.elapsed_time(e1)
+    per_system = []
     for i in pick:
         sx = torch.as_tensor(systems[i][0]).cuda()
         sq = torch.as_tensor(systems[i][1]).cuda()
@@ -246,6 +248,9 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
         floor = 0.5 * 2.837297479 * float(np.sum(systems[i][1] ** 2))
         rel.append(abs(E32[i] - U64) / max(abs(U64), floor))
         rel_raw.append(abs(E32[i] - U64) / abs(U64))
+        per_system.append({"system": int(i), "N": int(sizes[i]), "U_fp64": float(U64),
+                           "abs_err": float(abs(E32[i] - U64)), "rel_err": rel_raw[-1],
+                           "abs_U_over_floor": abs(U64) / floor})
     # the fit of the whole batch (one product over all 256 right-hand sides):
     # FP64 on the CUDA cores vs split-BF16 on the tensor cores (tcgen05)
     from paper_1806_04801_gb300 import hsma
@@ -277,9 +282,14 @@ def run_batched(plan_fp32, plan_fp64, steps: int, warmup: int, flush, fp64_syste
             "fp32_one_system_per_launch_systems_per_s": len(systems) / (t32_all / 1000.0),
             "sampled_systems_for_single_paths": int(len(pick)),
             "speedup_vs_fp64_single": t64_all / ms,
-            "max_rel_energy_err_vs_fp64": float(max(rel)),
-            "max_rel_energy_err_vs_fp64_unfloored": float(max(rel_raw)),
-            "energy_err_note": "denominator max(|U|, 1/2 |xi| sum q^2 / L), xi = -2.837297 (self-image scale)",
+            "max_rel_energy_err_vs_fp64": float(max(rel_raw)),
+            "max_rel_energy_err_vs_fp64_floored": float(max(rel)),
+            "max_rel_energy_err_vs_fp64_where_abs_U_above_floor": float(max(
+                [r["rel_err"] for r in per_system if r["abs_U_over_floor"] >= 1.0] or [0.0])),
+            "systems_over_1e-6": [r for r in per_system if r["rel_err"] > 1e-6],
+            "energy_err_note": ("plain |U32 - U64| / |U64| per system; floored: denominator max(|U|, 1/2 |xi| "
+                                "sum q^2 / L), xi = -2.837297 (the energy scale of the periodic self-images)"),
+            "per_system": per_system,
             "precision": f"{plan_fp32.precision}: fp32 pair sums ({'split-BF16 tensor-core' if plan_fp32.precision == 'fp32_tc' else 'fp64'} fit), CUDA graph",
             "fit_ms_per_batch": fit_ms,
             "tensor_core_fit_max_rel_energy_dev": float(fit_dev)}
@@ -387,6 +397,10 @@ def dist_env():
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks, power and throttle reasons during the timed region."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
     def __init__(self):
         self.path = None
         self.proc = None
@@ -394,17 +408,26 @@ class ClockSampler:
     def start(self, gpu_index: int):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
-    def stop(self) -> dict:
+    @staticmethod
+    def _stamp(field: str):
+        """nvidia-smi's local-time timestamp as seconds since the epoch, or None."""
+        import datetime
+        try:
+            return datetime.datetime.strptime(field.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, window=None) -> dict:
+        """Summary of the samples; window = (t0, t1) host times (time.time())
+        keeps the samples taken inside the timed region, when the rows carry
+        timestamps and some fall inside it."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -412,78 +435,87 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
+        rows, stamps = [], []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
+            t = self._stamp(parts[0]) if parts else None
+            if t is not None:
+                parts = parts[1:]
             if len(parts) >= 9:
                 rows.append(parts)
+                stamps.append(t)
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        in_window = False
+        if window is not None:
+            keep = [r for r, t in zip(rows, stamps) if t is not None and window[0] <= t <= window[1]]
+            if keep:
+                rows, in_window = keep, True
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         pw = [float(r[3]) for r in rows if r[3].replace(".", "", 1).isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons,
+                "samples_in_timed_region": in_window}
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(xyz, q, w, budget_s: float = 12.0, threads: int | None = None):
-    """Time the oracle (as it stands) on a bounded sample of the workload and
-    scale to systems/s: the monitoring-point sums and the fit are run in full,
-    the particle sums on a sample whose cost is extrapolated linearly in N."""
+def cpu_oracle_setup(xyz, q, w, threads: int | None = None):
+    """The oracle's plan (preparation step) for the workload, built outside
+    any timed region, and the thread count its sums use."""
     from oracle import hsma as oh
     threads = threads or os.cpu_count() or 1
     F2, _ = oh.fib_from_points(w.Q)
-    plan = oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2)
-    n = len(q)
+    return oh.make_plan(w.box, w.bc, w.p, w.R, w.Kmon, F2), threads
+
+
+def cpu_oracle_step(xyz, q, plan, threads: int):
+    """One complete FP64 update step of the oracle (as it stands: in-set,
+    near-field sums at every particle and monitoring point, least squares,
+    surface images, energy and forces), timed on the host clock."""
+    from oracle import hsma as oh
     t0 = time.perf_counter()
-    oh.energy_forces(xyz, q, plan, nthreads=threads, sample=np.arange(0, n, max(1, n // 16))[:16])
-    t_fixed = time.perf_counter() - t0
-    # particle sums: size a sample to fill the remaining budget
-    per_particle = None
-    k = 64
-    from oracle import coulomb, inset
-    c = oh.centre_positions(xyz, w.box, w.bc)
-    s_xyz, s_q, _, _ = inset(c, q, np.asarray(w.box, dtype=np.float64), w.bc, w.R)
-    while True:
-        idx = np.linspace(0, n - 1, k).astype(np.int64)
-        t0 = time.perf_counter()
-        coulomb(s_xyz, s_q, c[idx], tskip=idx, field=True, nthreads=threads)
-        dt = time.perf_counter() - t0
-        per_particle = dt / k
-        if dt > 1.0 or k >= n:
-            break
-        k = min(n, int(k * max(2.0, 1.5 / max(dt, 1e-3))))
-    t_system = t_fixed + per_particle * n
-    return {"systems_per_s": 1.0 / t_system, "threads": threads, "t_fixed_s": t_fixed,
-            "particles_sampled": int(k), "n_inset": int(s_xyz.shape[0]),
-            "pairs_per_s": (n * (s_xyz.shape[0] - 1)) / (per_particle * n)}
+    out = oh.energy_forces(xyz, q, plan, nthreads=threads)
+    return time.perf_counter() - t0, out
 
 
-def reference_arm(args, rank, world):
-    """--impl reference: the FP64 CPU oracle on the host cores, on a bounded
-    sample of the same workload, for each of W + K steps."""
+def reference_arm(args, rank, world, budget_s: float = 150.0):
+    """--impl reference: the FP64 CPU oracle on the host cores, complete
+    update steps of the same workload.  A step takes tens of seconds, so at
+    most as many of the requested steps are timed as fit in budget_s (at
+    least one); the line says how many.  Warm-up: the oracle's plan and one
+    call on 16 sampled particles (the W requested steps would each be a
+    full step)."""
     if rank != 0:
         return 0
+    from oracle import hsma as oh
     from paper_1806_04801_gb300 import inputs as I
     w = I.LARGE_PERIODIC
     xyz, q = I.large_periodic(args.n)
-    vals = []
-    for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(xyz, q, w, budget_s=4.0)
-        if i >= args.warmup:
-            vals.append(r["systems_per_s"])
-    v = statistics.median(vals)
-    sample = (f"per step: full monitoring-point sums + fit + 16 particles, then particle near-field sums on "
-              f"{r['particles_sampled']} of {args.n} particles extrapolated linearly in N")
+    plan, threads = cpu_oracle_setup(xyz, q, w)
+    oh.energy_forces(xyz, q, plan, nthreads=threads, sample=np.arange(16))
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < args.steps:
+        dt, out = cpu_oracle_step(xyz, q, plan, threads)
+        times.append(dt)
+        if time.perf_counter() - t_start + dt > budget_s:
+            break
+    total = sum(times)
+    v = len(times) / total
+    sample = (f"{len(times)} complete FP64 update steps of the N={args.n} workload (all particles, all "
+              f"monitoring points, fit, surface images), plan built outside the timed region")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "systems/s", "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
+            "warmup_note": "oracle plan + one call on 16 sampled particles",
+            "ms_per_step": 1000.0 * total / len(times), "step_s": times, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "N": args.n, "p": w.p, "Kmon": w.Kmon, "Q": w.Q, "Rs": w.R},
-            "cpu_baseline": {"value": v, "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
+            "energy": out["energy"], "n_inset": int(out["n_inset"]),
+            "cpu_baseline": {"value": v, "unit": "systems/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -586,6 +618,7 @@ def main():
     step_ms, pair_ms, launches0 = [], [], hsma.kernel_launches()
     n_inset = None
     wall0 = time.perf_counter()
+    epoch0 = time.time()
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -602,7 +635,7 @@ def main():
     launches = hsma.kernel_launches() - launches0
     if dist:
         dist.barrier()
-    clk = clocks.stop() if rank == 0 else None
+    clk = clocks.stop(window=(epoch0, time.time())) if rank == 0 else None
 
     total_ms = sum(step_ms)
     if dist:
@@ -621,7 +654,10 @@ def main():
     ops = OPS_POT_FIELD * pairs_pf + OPS_POT * pairs_p
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
-    peak_ops = sms * FP32_LANES_PER_SM * RECIPE_MAX_SM_MHZ * 1e6
+    # the lane peak at the SM clock sampled during the timed region (its
+    # median), else at the part's maximum clock
+    sm_mhz = (clk or {}).get("sm_mhz") or RECIPE_MAX_SM_MHZ
+    peak_ops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6
     achieved = ops / (pair_avg_ms / 1000.0)
 
     # end to end through the public API with host buffers (pinned)
@@ -683,11 +719,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is an N = 1 figure
         def cpu_baseline():
-            r = cpu_oracle_rate(xyz, q, w)
-            return {"value": r["systems_per_s"], "unit": "systems/s", "cores": r["threads"], "kind": "oracle",
-                    "sample": (f"full monitoring-point sums and fit, near-field particle sums on "
-                               f"{r['particles_sampled']} of {n} particles, extrapolated linearly in N"),
-                    "pairs_per_s": r["pairs_per_s"]}
+            cplan, threads = cpu_oracle_setup(xyz, q, w)
+            dt, out = cpu_oracle_step(xyz, q, cplan, threads)
+            return {"value": 1.0 / dt, "unit": "systems/s", "cores": threads, "kind": "oracle",
+                    "sample": (f"one complete FP64 update step of the N={n} workload (all {n} particles, "
+                               f"{nmon} monitoring targets, fit, surface images), plan built outside the timed "
+                               f"region"),
+                    "step_s": dt, "n_inset": int(out["n_inset"]),
+                    "pairs_per_s": (n * (out["n_inset"] - 1) + nmon * out["n_inset"]) / dt}
         cpu = side(cpu_baseline)
 
     if rank != 0:
@@ -713,7 +752,8 @@ def main():
                      "traffic": (PAIR_FP32_TRAFFIC_BYTES.get((n, tuning["pair_variant"], tuning["items_per_slot"]))
                                  if args.precision != "fp64" else None),
                      "pairs_per_s": (pairs_pf + pairs_p) / (pair_avg_ms / 1000.0),
-                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {RECIPE_MAX_SM_MHZ:.0f} MHz; "
+                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
+                                   f"sampled in the timed region); "
                                    f"{OPS_POT_FIELD} ops per potential+field pair, {OPS_POT} per potential pair",
                      "kernel_ms": pair_avg_ms, "share_of_step": pair_avg_ms / ms_per_step,
                      "measured_fp32": ({"scalar_fma": fp32_meas[0] / 1e12, "packed_fma": fp32_meas[1] / 1e12,

@@ -20,7 +20,7 @@ def _free_port() -> int:
 def test_reference_arm_under_torchrun_two_ranks():
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"]
+           "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "0", "--particles", "3000"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert out.returncode == 0, out.stderr[-3000:]
@@ -29,7 +29,10 @@ def test_reference_arm_under_torchrun_two_ranks():
     r = json.loads(lines[0])
     assert r["impl"] == "reference" and r["value"] > 0 and r["unit"] == "systems/s"
     assert r["cpu_baseline"]["kind"] == "oracle" and r["e2e"]["h2d_bytes_per_step"] == 0
-    assert r["config"]["N"] == 100_000
+    assert r["config"]["N"] == 3000
+    # complete oracle steps, each timed (as many of the requested as fit the time budget)
+    assert 1 <= r["steps"] <= 2 and len(r["step_s"]) == r["steps"] and r["steps_requested"] == 2
+    assert abs(r["ms_per_step"] - 1000.0 * sum(r["step_s"]) / r["steps"]) < 1e-6
 
 
 def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path):
@@ -89,3 +92,31 @@ def test_profile_commands_parse_with_the_current_bench(monkeypatch):
         if args.tuning:
             v, i = bench.fixed_tuning(args)
             assert v in (2, 4, 5, 12, 13, 14, 15, 16, 17) and i >= 1, (name, args.tuning)
+
+
+def test_clock_sampler_keeps_the_timed_region(tmp_path):
+    """With nvidia-smi's timestamp column, only samples inside the timed
+    region's host-time window enter the median."""
+    import datetime
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    t0 = 1_800_000_000.0
+    stamp = lambda t: datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]  # noqa: E731
+    rows = [f"{stamp(t0 - 1.0)}, 0, 1200, 2070, 200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            f"{stamp(t0 + 0.2)}, 0, 1965, 2070, 1300.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            f"{stamp(t0 + 0.4)}, 0, 1980, 2070, 1310.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            f"{stamp(t0 + 5.0)}, 0, 1100, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler()
+    cs.path, cs.proc = str(path), _Done()
+    r = cs.stop(window=(t0, t0 + 1.0))
+    assert r["samples"] == 2 and r["samples_in_timed_region"] and r["sm_mhz"] == 1972.5

@@ -219,22 +219,30 @@ int hsma_energy_forces_batched(hsma_plan_t plan, int nsys, const int64_t *offset
  *      near-field sums over the whole in-set), and Phi_in at the owned
  *      monitoring targets, written into phi_mon (host, n_mon_targets, in the
  *      order of hsma_plan_get_matrix(0); zero outside the owned slice).
- *   2. The caller sums phi_mon over the parts (an all-reduce, or all-gather,
- *      of n_mon_targets doubles).
+ *      Outputs (host arrays of capacity n): index[j] is the caller's index of
+ *      the j-th owned particle, phi[j] its Phi_in and field[3j..3j+2] its
+ *      E_in; *count receives the number of owned particles.
+ *   2. The caller sums phi_mon over the parts (an all-reduce of
+ *      n_mon_targets doubles).
  *   3. hsma_shard_far: the fit from the full phi_mon (the same on every
- *      part), the surface images (or series) and Phi_out, E_out at the owned
- *      particles.
- *   4. The caller forms U = 1/2 sum q_i (phi_in + phi_out) over its particles
- *      and all-reduces it; F_i = q_i (E_in + E_out).
+ *      part), the surface images (or series), Phi_out and E_out at the owned
+ *      particles, and -- on the device, from phi_in / field_in, the near
+ *      stage's phi / field of this part (host, count_in = the near stage's
+ *      *count entries, owned order; another count_in is HSMA_E_ARG) -- the
+ *      owned particles' potentials pot[j] = Phi_in + Phi_out, forces
+ *      forces[3j..3j+2] = q (E_in + E_out), and the part's energy
+ *      *energy = 1/2 sum_j q_j pot[j] (FP64, fixed summation order).  index
+ *      and count as in stage 1 (the same slice).
+ *   4. The caller sums *energy over the parts (an all-reduce of one double):
+ *      U of Sec. II.C.  Forces stay with the part that owns the particle.
  *
- * Outputs are host arrays of capacity n: index[j] is the caller's index of
- * the j-th owned particle, phi[j] and field[3j..3j+2] its values; *count
- * receives the number of owned particles (the same slice in both stages).
- * x_q may be host or device.  Errors as hsma_energy_forces. */
+ * x_q may be host or device; every other array is host memory.  Errors as
+ * hsma_energy_forces. */
 int hsma_shard_near(hsma_plan_t plan, const hsma_particles *x_q, int part, int nparts, int64_t *index,
                     double *phi, double *field, int64_t *count, double *phi_mon);
-int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *phi_mon, int part, int nparts,
-                   int64_t *index, double *phi, double *field, int64_t *count);
+int hsma_shard_far(hsma_plan_t plan, const hsma_particles *x_q, const double *phi_mon, const double *phi_in,
+                   const double *field_in, int64_t count_in, int part, int nparts, int64_t *index, double *pot,
+                   double *forces, int64_t *count, double *energy);
 
 /* ----------------------------------------------------------------- tuning */
 /* Work decomposition of the near-field pair kernel (no counterpart in the
@@ -385,6 +393,8 @@ int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tg
  * threads -- race on it and give wrong results, so serialise them.  The first
  * call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is looked up again whenever the current context is a new one
+ * (after a cudaDeviceReset, say), so the entry point stays usable then.
  * Returns once pot/field hold the results.
  * Errors: HSMA_E_ARG, HSMA_E_CAPACITY, HSMA_E_TIMEOUT, HSMA_E_CUDA. */
 int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const double *tgt, double *pot,
@@ -412,6 +422,12 @@ const char *hsma_version(void);
 /* Number of kernel launches this library has issued (all plans, all
  * threads) since it was loaded; graph replays count each kernel node. */
 int64_t hsma_kernel_launches(void);
+
+/* Number of device and pinned-host allocation and free calls (cudaMalloc,
+ * cudaFree, cudaMallocHost, cudaFreeHost) this library has made since it was
+ * loaded, over all plans and threads: a caller can check with it that a call
+ * allocated nothing (no counterpart in the paper). */
+int64_t hsma_allocation_calls(void);
 
 /* Per-phase device times (milliseconds) of the plan's last update step,
  * when opts.profile was set: [0] in-set, [1] near-field pair sums,

@@ -18,6 +18,7 @@
 namespace hsma {
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_alloc_calls{0};
 static thread_local char g_cuda_err[384];
 
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line)
@@ -211,11 +212,11 @@ int map_status(int st)
 int ensure_pinned(hsma_plan_s *p, size_t bytes)
 {
     if (bytes <= p->hpin_cap) return HSMA_OK;
-    if (p->hpin) cudaFreeHost(p->hpin);
+    if (p->hpin) host_free(p->hpin);
     p->hpin = nullptr;
     p->hpin_cap = 0;
     size_t nb = std::max(bytes, (size_t)65536);
-    HSMA_CUDA_TRY(cudaMallocHost(&p->hpin, nb));
+    HSMA_CUDA_TRY(host_malloc(&p->hpin, nb));
     p->hpin_cap = nb;
     return HSMA_OK;
 }
@@ -395,15 +396,15 @@ int ensure_workspace(hsma_plan_s *p, size_t bytes)
     if (bytes <= p->ws_cap) return HSMA_OK;
     if (p->ws_mem) {
         HSMA_CUDA_TRY(cudaStreamSynchronize(p->stream));
-        cudaFree(p->ws_mem);
+        dev_free(p->ws_mem);
     }
     p->ws_mem = nullptr;
     p->ws_cap = 0;
     size_t nb = align_up(bytes + bytes / 8, 1 << 20);
-    cudaError_t e = cudaMalloc(&p->ws_mem, nb);
+    cudaError_t e = dev_malloc(&p->ws_mem, nb);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        e = cudaMalloc(&p->ws_mem, bytes);
+        e = dev_malloc(&p->ws_mem, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p->ws_mem = nullptr;
@@ -548,8 +549,8 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
         record(p, st, 6);
     }
     if ((rc = launch_finalize(w.sys, nsys, sh.max_n, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
-                              want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, w.upart, w.energy, w.status,
-                              st)))
+                              want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, nullptr, w.upart, w.energy,
+                              w.status, st)))
         return rc;
     record(p, st, 7);
     return HSMA_OK;
@@ -755,13 +756,13 @@ __global__ void shard_gather_kernel(long long lo, long long cnt, const int *perm
 // One stage of the target-sharded update step for part `part` of `nparts`
 // (see hsma_shard_near / hsma_shard_far).  Single system; host outputs.
 int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part, int nparts,
-              const double *phi_mon_in, double *phi_mon_out, int64_t *index, double *phi, double *field,
-              int64_t *count)
+              const double *phi_mon_in, const double *phi_in, const double *field_in, int64_t count_in,
+              double *phi_mon_out, int64_t *index, double *phi, double *field, int64_t *count, double *energy)
 {
     if (!p || !x || !x->xyz || !x->q || x->n < 1 || nparts < 1 || part < 0 || part >= nparts || !index || !phi ||
         !field || !count)
         return HSMA_E_ARG;
-    if (far_stage ? !phi_mon_in : !phi_mon_out) return HSMA_E_ARG;
+    if (far_stage ? (!phi_mon_in || !phi_in || !field_in || !energy) : !phi_mon_out) return HSMA_E_ARG;
     const long long n = x->n;
     if (n > kMaxInsetSlots / p->nshifts) return HSMA_E_ARG;
     const int prec = p->precision;
@@ -841,6 +842,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
     if ((rc = launch_inset(ia, st))) return rc;
 
     const long long cnt = t_hi - t_lo;
+    if (far_stage && count_in != cnt) return HSMA_E_ARG;  // not this part's near-stage arrays
     std::vector<double> mon(p->nmon);
     if (!far_stage) {
         if (w.boxes && (rc = launch_tile_boxes(w.sys, 1, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
@@ -896,24 +898,34 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
                                           p->dirs, w.img, p->Rs, p->dr, prec, w.phi_out, w.e_out, st);
         }
         if (rc) return rc;
+        // the near stage's Phi_in, E_in of the owned particles into their
+        // target slots, then potentials, forces and the part's energy
+        // 1/2 sum q_i (Phi_in + Phi_out) on the device (owned order)
         if (cnt > 0) {
-            shard_gather_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(t_lo, cnt, w.perm, w.phi_out,
-                                                                                w.e_out, w.idx64, w.pot, w.forces);
-            HSMA_LAUNCHED();
+            HSMA_CUDA_TRY(cudaMemcpyAsync(w.phi_tgt + t_lo, phi_in, sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                                          st));
+            HSMA_CUDA_TRY(cudaMemcpyAsync(w.e_part + 3 * t_lo, field_in, sizeof(double) * 3 * cnt,
+                                          cudaMemcpyHostToDevice, st));
         }
+        if ((rc = launch_finalize(w.sys, 1, std::max<long long>(cnt, 1), w.perm, w.q, w.phi_tgt, w.e_part,
+                                  w.phi_out, w.e_out, w.forces, w.pot, w.idx64, w.upart, w.energy, w.status, st)))
+            return rc;
     }
     std::vector<long long> idx(std::max<long long>(cnt, 1));
     int hst = 0;
+    double u_part = 0.0;
     if (cnt > 0) {
         HSMA_CUDA_TRY(cudaMemcpyAsync(idx.data(), w.idx64, sizeof(long long) * cnt, cudaMemcpyDeviceToHost, st));
         HSMA_CUDA_TRY(cudaMemcpyAsync(phi, w.pot, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
         HSMA_CUDA_TRY(cudaMemcpyAsync(field, w.forces, sizeof(double) * 3 * cnt, cudaMemcpyDeviceToHost, st));
     }
+    if (far_stage) HSMA_CUDA_TRY(cudaMemcpyAsync(&u_part, w.energy, sizeof(double), cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaMemcpyAsync(&hst, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     HSMA_CUDA_TRY(cudaStreamSynchronize(st));
     HSMA_CUDA_TRY(cudaGetLastError());
     for (long long j = 0; j < cnt; ++j) index[j] = idx[j];
     *count = cnt;
+    if (far_stage) *energy = u_part;
     if (!far_stage) {
         for (int k = 0; k < p->nmon; ++k) phi_mon_out[k] = 0.0;
         for (long long k = m_lo; k < m_hi; ++k) phi_mon_out[p->mon_perm[k]] = mon[k];
@@ -988,7 +1000,7 @@ void hsma::plan_trim_workspace(hsma_plan_t p, size_t max_keep)
         p->graph_exec = nullptr;
         p->graph_key.clear();
     }
-    cudaFree(p->ws_mem);
+    dev_free(p->ws_mem);
     p->ws_mem = nullptr;
     p->ws_cap = 0;
     p->ws = Workspace();
@@ -1034,6 +1046,8 @@ const char *hsma_strerror(int code)
 }
 
 int64_t hsma_kernel_launches(void) { return g_launches.load(); }
+
+int64_t hsma_allocation_calls(void) { return g_alloc_calls.load(); }
 
 int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, int Q, int Kmon, const hsma_opts *opts)
 {
@@ -1128,7 +1142,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         pl->tc_lo = c.take<char>(tc_operand_bytes(K, ncols));
         pl->tc_mdf = c.take<char>(tc_residual_matrix_bytes(K, ncols));
         if (pass == 0) {
-            if (cudaMalloc(&pl->plan_mem, align_up(c.off, 256)) != cudaSuccess) {
+            if (dev_malloc(&pl->plan_mem, align_up(c.off, 256)) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(HSMA_E_OOM);
             }
@@ -1137,7 +1151,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
     // temporaries for the basis at monitoring points and the column-major M
     double *Bx = nullptr, *Mcol = nullptr;
     size_t tmp_bytes = sizeof(double) * ((size_t)nmon * Nb + (size_t)K * ncols);
-    if (cudaMalloc(&Bx, tmp_bytes) != cudaSuccess) {
+    if (dev_malloc(&Bx, tmp_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(HSMA_E_OOM);
     }
@@ -1198,7 +1212,7 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
             break;
         }
     } while (0);
-    cudaFree(Bx);
+    dev_free(Bx);
     if (rc) return fail(rc);
     pl->cond = cond;
     if (!rank_ok || !(cond < 1e15)) return fail(HSMA_E_ILLCOND);
@@ -1221,9 +1235,9 @@ void hsma_plan_destroy(hsma_plan_t pl)
     if (pl->order_ev) cudaEventDestroy(pl->order_ev);
     if (pl->events_ready)
         for (int i = 0; i < 8; ++i) cudaEventDestroy(pl->ev[i]);
-    if (pl->ws_mem) cudaFree(pl->ws_mem);
-    if (pl->plan_mem) cudaFree(pl->plan_mem);
-    if (pl->hpin) cudaFreeHost(pl->hpin);
+    if (pl->ws_mem) dev_free(pl->ws_mem);
+    if (pl->plan_mem) dev_free(pl->plan_mem);
+    if (pl->hpin) host_free(pl->hpin);
     cudaGetLastError();
     delete pl;
 }
@@ -1402,13 +1416,16 @@ int64_t hsma_last_get(hsma_plan_t pl, int which, double *host_out, int64_t count
 int hsma_shard_near(hsma_plan_t pl, const hsma_particles *x, int part, int nparts, int64_t *index, double *phi,
                     double *field, int64_t *count, double *phi_mon)
 {
-    return run_shard(pl, x, false, part, nparts, nullptr, phi_mon, index, phi, field, count);
+    return run_shard(pl, x, false, part, nparts, nullptr, nullptr, nullptr, 0, phi_mon, index, phi, field, count,
+                     nullptr);
 }
 
-int hsma_shard_far(hsma_plan_t pl, const hsma_particles *x, const double *phi_mon, int part, int nparts,
-                   int64_t *index, double *phi, double *field, int64_t *count)
+int hsma_shard_far(hsma_plan_t pl, const hsma_particles *x, const double *phi_mon, const double *phi_in,
+                   const double *field_in, int64_t count_in, int part, int nparts, int64_t *index, double *pot,
+                   double *forces, int64_t *count, double *energy)
 {
-    return run_shard(pl, x, true, part, nparts, phi_mon, nullptr, index, phi, field, count);
+    return run_shard(pl, x, true, part, nparts, phi_mon, phi_in, field_in, count_in, nullptr, index, pot, forces,
+                     count, energy);
 }
 
 // ------------------------------------------------------------------ tuning
@@ -1611,7 +1628,7 @@ int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tg
         bytes = align_up(cc.off, 256);
     }
     void *mem = nullptr;
-    HSMA_CUDA_TRY(cudaMalloc(&mem, bytes));
+    HSMA_CUDA_TRY(dev_malloc(&mem, bytes));
     Carver cc(mem);
     float4 *shi = cc.take<float4>(ns);
     float4 *slo = cc.take<float4>(ns);
@@ -1674,7 +1691,7 @@ int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tg
         if (!rc && cudaMemcpy(&hst, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HSMA_E_CUDA;
         if (!rc) rc = map_status(hst);
     } while (0);
-    cudaFree(mem);
+    dev_free(mem);
     if (rc == HSMA_OK && cudaGetLastError() != cudaSuccess) rc = HSMA_E_CUDA;
     return rc;
 }
@@ -1686,13 +1703,13 @@ int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, voi
     auto nt = norm_table(p);
     double *dn = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
-    HSMA_CUDA_TRY(cudaMalloc(&dn, sizeof(double) * Nb));
+    HSMA_CUDA_TRY(dev_malloc(&dn, sizeof(double) * Nb));
     int rc = HSMA_OK;
     if (cudaMemcpyAsync(dn, nt.data(), sizeof(double) * Nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = HSMA_E_CUDA;
     if (!rc) rc = launch_basis(p, Rs, np, pts, 3, dn, out, Nb, st);
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
-    cudaFree(dn);
+    dev_free(dn);
     return rc;
 }
 

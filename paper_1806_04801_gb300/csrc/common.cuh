@@ -25,6 +25,33 @@ extern std::atomic<long long> g_launches;  // kernels issued by this library
 
 #define HSMA_LAUNCHED() hsma::g_launches.fetch_add(1, std::memory_order_relaxed)
 
+// Every device and pinned-host allocation or free of this library goes
+// through these wrappers, which count the calls (hsma_allocation_calls), so
+// that a test can show that an entry point allocates nothing.
+extern std::atomic<long long> g_alloc_calls;
+template <class T>
+inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+inline cudaError_t dev_free(void *p)
+{
+    g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+    return cudaFree(p);
+}
+template <class T>
+inline cudaError_t host_malloc(T **p, size_t bytes)
+{
+    g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+    return cudaMallocHost(reinterpret_cast<void **>(p), bytes);
+}
+inline cudaError_t host_free(void *p)
+{
+    g_alloc_calls.fetch_add(1, std::memory_order_relaxed);
+    return cudaFreeHost(p);
+}
+
 void set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
 // Device status bits, one int per system; the host maps them to codes.
@@ -82,6 +109,19 @@ __device__ __forceinline__ float2 df_add_df(float2 a, float2 b)
     e = __fadd_rn(e, __fadd_rn(a.y, b.y));
     const float h = __fadd_rn(s, e);
     return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+// Right-hand side of the least-squares fit at monitoring point i (Sec. II.A):
+// periodic b_i = Phi_in(x~_i) - Phi_in(x_i) (the periodicity residual),
+// grounded b_i = -Phi_in(x_i).  ph: the monitoring-target potentials of one
+// system (the K points, then their K partners), in the pair kernel's target
+// order; inv maps a point's index to its slot there (nullptr: identity).
+__device__ __forceinline__ double rhs_at(const double *ph, const int *inv, int K, int i, bool periodic)
+{
+    const int a = inv ? inv[i] : i;
+    if (!periodic) return -ph[a];
+    const int b = inv ? inv[K + i] : K + i;
+    return ph[b] - ph[a];
 }
 
 // Reciprocal square root on the special-function unit.
@@ -350,13 +390,16 @@ int launch_series_field(const SysDesc *sys, int nsys, long long max_n, int P, do
 int finalize_blocks(long long max_n);
 int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *perm, const double *q,
                     const double *phi_tgt, const double *e_part, const double *phi_out, const double *e_out,
-                    double *forces, double *pot, double *upart, double *energy, int *status, cudaStream_t st);
+                    double *forces, double *pot, long long *owned_idx, double *upart, double *energy, int *status,
+                    cudaStream_t st);
 
 // api.cu: free a plan's workspace when it holds more than max_keep bytes
 // (used by the serving lanes to stay inside their memory budget).
 void plan_trim_workspace(hsma_plan_t plan, size_t max_keep);
 
-// tc_fit.cu
+// tc_fit.cu: the tensor-core fit.  Mp_hi / Mp_lo: M+ as two BF16 words;
+// Mdf: M (K x n_cols) as FP32 word pairs (prepare_tc_operands fills all of
+// them at plan time).
 int launch_fit_tc(const SysDesc *sys, int nsys, int bc, int K, int ncols, int Nb, const void *Mp_hi,
                   const void *Mp_lo, const void *Mdf, const double *phi_tgt, const int *mon_inv, double *b_out,
                   double *A, float *work, int *status, int sms, cudaStream_t st);

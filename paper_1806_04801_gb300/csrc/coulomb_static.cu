@@ -18,7 +18,10 @@
 //
 // The first call on each device looks up the array's device address with
 // cudaGetSymbolAddress (host code cannot use the symbol itself as a device
-// pointer) and caches it; make that first call before any stream capture.
+// pointer) and caches it with the identity of the current context; make that
+// first call before any stream capture.  A later call in a different context
+// (the device was reset, and the module loaded again) looks it up anew.
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
 
@@ -37,7 +40,35 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address belongs to
 int g_num_sms[kMaxDevices] = {};
+
+// Process-unique id of the current context (cuCtxGetId), reached through the
+// runtime's driver entry-point table so that the library needs no link
+// against the driver library.  Returns false where the driver lacks it.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -128,18 +159,25 @@ __global__ void static_scatter_kernel(long long n, const double *phi, const doub
     }
 }
 
-// Once per device: the static array's device address and the SM count.
+// Once per device and context: the static array's device address and the
+// SM count, looked up with the device current (the lookup itself makes the
+// runtime's context current on a first call).  Without a context id from the
+// driver, the address is looked up on every call.
 int static_setup(int dev, void **addr, int *sms)
 {
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (dev < 0 || dev >= kMaxDevices) return HSMA_E_ARG;
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;
+    bool have_ctx = current_context_id(&ctx);
+    if (!g_scratch_addr[dev] || !have_ctx || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         HSMA_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
         int n = 0;
         HSMA_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        have_ctx = current_context_id(&ctx);
         g_num_sms[dev] = n;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = have_ctx ? ctx : 0;
     }
     *addr = g_scratch_addr[dev];
     *sms = g_num_sms[dev];

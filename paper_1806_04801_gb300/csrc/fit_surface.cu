@@ -20,14 +20,6 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
-__device__ __forceinline__ double rhs_at(const double *ph, const int *inv, int K, int i, bool periodic)
-{
-    const int a = inv ? inv[i] : i;
-    if (!periodic) return -ph[a];
-    const int b = inv ? inv[K + i] : K + i;
-    return ph[b] - ph[a];
-}
-
 __global__ void fit_fp64_kernel(const SysDesc *sys, int bc, int K, int ncols, int Nb, const double *Mp,
                                 const double *phi_tgt, const int *mon_inv, double *b_out, double *A)
 {
@@ -342,28 +334,38 @@ __global__ void __launch_bounds__(kSurf64Threads) surface_pairs_fp64_kernel(
     }
 }
 
-// Forces, potentials and per-block energy partials.  Target i of a system is
-// its i-th particle in spatial order; perm maps it back to the caller's index.
-// Block b of system s covers particles [b * kFinal, (b + 1) * kFinal).
+// Forces, potentials and per-block energy partials of the particles a call
+// owns: the sorted range [sp_lo, sp_lo + sp_n) of each system (all of it,
+// except for a part of a target-sharded step).  Target i of a system is its
+// i-th particle in spatial order; perm maps it back to the caller's index.
+// Block b of system s covers particles [sp_lo + b kFinal, sp_lo + (b + 1) kFinal).
+// owned_idx == nullptr: outputs at the caller's indices; otherwise (one
+// system) output j is particle sp_lo + j and owned_idx[j] its caller index.
 constexpr int kFinalThreads = 256;
 constexpr int kFinal = 2048;
 
 __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const SysDesc *sys, const int *perm, const double *q,
                                                                  const double *phi_tgt, const double *e_part,
                                                                  const double *phi_out, const double *e_out,
-                                                                 double *forces, double *pot, double *upart,
-                                                                 int nb_max, int *status)
+                                                                 double *forces, double *pot, long long *owned_idx,
+                                                                 double *upart, int nb_max, int *status)
 {
     __shared__ double red[32];
     const int s = blockIdx.y;
     const SysDesc sd = sys[s];
-    const long long i0 = (long long)blockIdx.x * kFinal;
+    const long long i0 = sd.sp_lo + (long long)blockIdx.x * kFinal;
+    const long long i1 = sd.sp_lo + sd.sp_n;
     double u = 0.0;
     bool bad = false;
-    for (long long i = i0 + threadIdx.x; i < sd.n && i < i0 + kFinal; i += blockDim.x) {
+    for (long long i = i0 + threadIdx.x; i < i1 && i < i0 + kFinal; i += blockDim.x) {
         long long t = sd.tgt_off + i, so = sd.part_off + i;
-        long long o = sd.part_off + perm[so];
-        double qi = q[o];
+        const long long ci = sd.part_off + perm[so];  // caller's index
+        double qi = q[ci];
+        long long o = ci;
+        if (owned_idx) {
+            o = i - sd.sp_lo;
+            owned_idx[o] = perm[so];
+        }
         double ph = phi_tgt[t] + phi_out[so];
         double ex = e_part[3 * t] + e_out[3 * so];
         double ey = e_part[3 * t + 1] + e_out[3 * so + 1];
@@ -382,13 +384,13 @@ __global__ void __launch_bounds__(kFinalThreads) finalize_kernel(const SysDesc *
     if (threadIdx.x == 0) upart[(long long)s * nb_max + blockIdx.x] = u;
 }
 
-// U = 1/2 sum of the block partials, in block order.
+// U = 1/2 sum of the block partials, in block order (of the owned range).
 __global__ void energy_kernel(const SysDesc *sys, const double *upart, int nb_max, double *energy, int *status)
 {
     const int s = blockIdx.x;
     if (threadIdx.x != 0) return;
     const SysDesc sd = sys[s];
-    const int nb = (int)((sd.n + kFinal - 1) / kFinal);
+    const int nb = (int)((sd.sp_n + kFinal - 1) / kFinal);
     double u = 0.0;
     for (int b = 0; b < nb; ++b) u += upart[(long long)s * nb_max + b];
     energy[s] = 0.5 * u;
@@ -441,11 +443,12 @@ int finalize_blocks(long long max_n) { return (int)((max_n + kFinal - 1) / kFina
 
 int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *perm, const double *q,
                     const double *phi_tgt, const double *e_part, const double *phi_out, const double *e_out,
-                    double *forces, double *pot, double *upart, double *energy, int *status, cudaStream_t st)
+                    double *forces, double *pot, long long *owned_idx, double *upart, double *energy, int *status,
+                    cudaStream_t st)
 {
     const int nb_max = finalize_blocks(max_n);
     finalize_kernel<<<dim3(nb_max, nsys), kFinalThreads, 0, st>>>(sys, perm, q, phi_tgt, e_part, phi_out, e_out,
-                                                                  forces, pot, upart, nb_max, status);
+                                                                  forces, pot, owned_idx, upart, nb_max, status);
     HSMA_LAUNCHED();
     energy_kernel<<<nsys, 32, 0, st>>>(sys, upart, nb_max, energy, status);
     HSMA_LAUNCHED();

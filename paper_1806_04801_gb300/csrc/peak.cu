@@ -68,7 +68,7 @@ extern "C" int hsma_fp32_peak(double *scalar_lane_ops_per_s, double *packed_lane
         if (e != cudaSuccess && rc == HSMA_OK) rc = HSMA_E_CUDA;
         return rc == HSMA_OK;
     };
-    if (cuda_ok(cudaMalloc(&out, sizeof(float) * grid * kPeakThreads)) &&
+    if (cuda_ok(dev_malloc(&out, sizeof(float) * grid * kPeakThreads)) &&
         cuda_ok(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) && cuda_ok(cudaEventCreate(&e0)) &&
         cuda_ok(cudaEventCreate(&e1))) {
         double best[2] = {0.0, 0.0};
@@ -96,6 +96,6 @@ extern "C" int hsma_fp32_peak(double *scalar_lane_ops_per_s, double *packed_lane
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (st) cudaStreamDestroy(st);
-    if (out) cudaFree(out);
+    if (out) dev_free(out);
     return rc;
 }

@@ -400,18 +400,18 @@ int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond_ho
         ~Temporaries()
         {
             for (void **q : p)
-                if (*q) cudaFree(*q);
+                if (*q) dev_free(*q);
         }
     } temps{{(void **)&scale, (void **)&rank_ok, (void **)&Q1, (void **)&Rinv}};
     size_t nd = (size_t)n;
-    HSMA_CUDA_TRY(cudaMalloc(&scale, nd * 4 * sizeof(double) + sizeof(double) + 16));
+    HSMA_CUDA_TRY(dev_malloc(&scale, nd * 4 * sizeof(double) + sizeof(double) + 16));
     vtop = scale + nd;
     vv = vtop + nd;
     diag = vv + nd;
     cond = diag + nd;
-    HSMA_CUDA_TRY(cudaMalloc(&rank_ok, sizeof(int)));
-    HSMA_CUDA_TRY(cudaMalloc(&Q1, (size_t)K * n * sizeof(double)));
-    HSMA_CUDA_TRY(cudaMalloc(&Rinv, (size_t)n * n * sizeof(double)));
+    HSMA_CUDA_TRY(dev_malloc(&rank_ok, sizeof(int)));
+    HSMA_CUDA_TRY(dev_malloc(&Q1, (size_t)K * n * sizeof(double)));
+    HSMA_CUDA_TRY(dev_malloc(&Rinv, (size_t)n * n * sizeof(double)));
     int one = 1;
     HSMA_CUDA_TRY(cudaMemcpyAsync(rank_ok, &one, sizeof(int), cudaMemcpyHostToDevice, st));
     equilibrate_kernel<<<n, 256, 0, st>>>(Wcol, K, scale, rank_ok);

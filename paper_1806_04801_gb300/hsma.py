@@ -87,6 +87,7 @@ SIGNATURES = {
     "hsma_strerror": (ctypes.c_char_p, [_I]),
     "hsma_version": (ctypes.c_char_p, []),
     "hsma_kernel_launches": (_I64, []),
+    "hsma_allocation_calls": (_I64, []),
     "hsma_fp32_peak": (_I, [_VP, _VP]),
     "hsma_last_timings": (_I, [_VP, _VP, _I]),
     "hsma_last_get": (_I64, [_VP, _I, _VP, _I64]),
@@ -97,8 +98,8 @@ SIGNATURES = {
     "hsma_plan_load_tuning": (_I, [_VP, ctypes.c_char_p]),
     "hsma_shard_near": (_I, [_VP, ctypes.POINTER(hsma_particles), _I, _I, _VP, _VP, _VP,
                              ctypes.POINTER(_I64), _VP]),
-    "hsma_shard_far": (_I, [_VP, ctypes.POINTER(hsma_particles), _VP, _I, _I, _VP, _VP, _VP,
-                            ctypes.POINTER(_I64)]),
+    "hsma_shard_far": (_I, [_VP, ctypes.POINTER(hsma_particles), _VP, _VP, _VP, _I64, _I, _I, _VP, _VP, _VP,
+                            ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)]),
 }
 
 _LIB = None
@@ -195,6 +196,11 @@ def _stream_handle(stream):
 def kernel_launches() -> int:
     """hsma_kernel_launches: kernels this library has launched (graph nodes counted on replay)."""
     return int(_lib().hsma_kernel_launches())
+
+
+def allocation_calls() -> int:
+    """hsma_allocation_calls: device and pinned-host allocation and free calls this library has made."""
+    return int(_lib().hsma_allocation_calls())
 
 
 def fp32_peak() -> tuple:
@@ -384,21 +390,29 @@ class Plan:
         k = cnt.value
         return idx[:k].copy(), phi[:k].copy(), fld[:k].copy(), mon
 
-    def shard_far(self, xyz, q, phi_mon, part: int, nparts: int):
-        """hsma_shard_far: (index, phi_out, E_out) for this part."""
+    def shard_far(self, xyz, q, phi_mon, phi_in, e_in, part: int, nparts: int):
+        """hsma_shard_far: (index, potentials, forces, energy of the part) for
+        this part, from the summed monitoring potentials and the part's
+        near-stage Phi_in, E_in (owned order)."""
         part_s, n = self._shard_args(xyz, q)
         mon = np.ascontiguousarray(phi_mon, dtype=np.float64)
         if mon.shape != (self.info()["n_mon_targets"],):
             raise ValueError("phi_mon must hold one value per monitoring target")
+        pin = np.ascontiguousarray(phi_in, dtype=np.float64)
+        ein = np.ascontiguousarray(e_in, dtype=np.float64)
+        if pin.ndim != 1 or pin.shape[0] > n or ein.shape != (pin.shape[0], 3):
+            raise ValueError("phi_in / e_in must be the near stage's arrays of this part (k and k x 3)")
         idx = np.empty(n, dtype=np.int64)
-        phi = np.empty(n)
-        fld = np.empty((n, 3))
+        pot = np.empty(n)
+        frc = np.empty((n, 3))
         cnt = ctypes.c_int64()
-        _check(_lib().hsma_shard_far(self._h, ctypes.byref(part_s), mon.ctypes.data, int(part), int(nparts),
-                                     idx.ctypes.data, phi.ctypes.data, fld.ctypes.data, ctypes.byref(cnt)),
+        u = ctypes.c_double()
+        _check(_lib().hsma_shard_far(self._h, ctypes.byref(part_s), mon.ctypes.data, pin.ctypes.data,
+                                     ein.ctypes.data, int(pin.shape[0]), int(part), int(nparts), idx.ctypes.data,
+                                     pot.ctypes.data, frc.ctypes.data, ctypes.byref(cnt), ctypes.byref(u)),
                "hsma_shard_far")
         k = cnt.value
-        return idx[:k].copy(), phi[:k].copy(), fld[:k].copy()
+        return idx[:k].copy(), pot[:k].copy(), frc[:k].copy(), u.value
 
     # ------------------------------------------------------------ tuning
     def set_tuning(self, pair_variant=None, items_per_slot=None):

@@ -7,16 +7,20 @@ parameters.  The update step (Sec. II.C) then needs only two small exchanges:
      and of the monitoring points);
   2. sum of the monitoring potentials over the ranks (n_mon_targets doubles);
   3. fit, surface images and far field at the rank's own particles (the fit
-     is repeated on every rank: it is tiny);
-  4. sum of the energy over the ranks (one double).  Forces stay with the rank
-     that owns the particle (gather them if the caller wants them in one
-     place).
+     is repeated on every rank: it is tiny), then -- on the device -- the
+     owned particles' potentials, forces and the part's energy;
+  4. sum of the parts' energies over the ranks (one double).  Forces stay
+     with the rank that owns the particle (gather them if the caller wants
+     them in one place).
 
-The compute backend is any object with ``near(xyz, q, part, nparts)`` ->
-(index, phi_in, E_in, phi_mon) and ``far(xyz, q, phi_mon, part, nparts)`` ->
-(index, phi_out, E_out); ``GpuBackend`` wraps a plan of the CUDA library.
-The communicator needs ``allreduce_sum(numpy array) -> numpy array``;
-``TorchComm`` uses torch.distributed (NCCL or gloo).
+This module does none of the method's arithmetic: it moves arrays between
+the stages and calls the all-reduce.  The compute backend is any object with
+``near(xyz, q, part, nparts)`` -> (index, phi_in, E_in, phi_mon) and
+``far(xyz, q, phi_mon, phi_in, E_in, part, nparts)`` -> (index, potentials,
+forces, energy of the part); ``GpuBackend`` wraps a plan of the CUDA library
+(hsma_shard_near / hsma_shard_far).  The communicator needs
+``allreduce_sum(numpy array) -> numpy array``; ``TorchComm`` uses
+torch.distributed (NCCL or gloo).
 """
 from __future__ import annotations
 
@@ -33,9 +37,10 @@ class GpuBackend:
         """Stage 1 on this rank's slice (hsma_shard_near): owned indices, Phi_in, E_in and the monitoring potentials."""
         return self.plan.shard_near(xyz, q, part, nparts)
 
-    def far(self, xyz, q, phi_mon, part, nparts):
-        """Stage 3 on this rank's slice (hsma_shard_far) from the summed monitoring potentials."""
-        return self.plan.shard_far(xyz, q, phi_mon, part, nparts)
+    def far(self, xyz, q, phi_mon, phi_in, e_in, part, nparts):
+        """Stage 3 on this rank's slice (hsma_shard_far): potentials, forces and the part's energy, from the
+        summed monitoring potentials and this part's near-stage results."""
+        return self.plan.shard_far(xyz, q, phi_mon, phi_in, e_in, part, nparts)
 
 
 class TorchComm:
@@ -72,38 +77,35 @@ def shard_update(backend, xyz, q, comm, part=None, nparts=None):
     forces of the owned particles, potentials of the owned particles)."""
     part = comm.rank if part is None else part
     nparts = comm.size if nparts is None else nparts
-    q_host = np.asarray(q.cpu().numpy() if hasattr(q, "cpu") else q, dtype=np.float64)
     idx, phi_in, e_in, phi_mon = backend.near(xyz, q, part, nparts)
     phi_mon = comm.allreduce_sum(phi_mon)
-    idx2, phi_out, e_out = backend.far(xyz, q, phi_mon, part, nparts)
+    idx2, pot, forces, u_part = backend.far(xyz, q, phi_mon, phi_in, e_in, part, nparts)
     if not np.array_equal(idx, idx2):
         raise RuntimeError("near and far stages disagree on the owned particles")
-    qi = q_host[idx]
-    pot = phi_in + phi_out
-    u = comm.allreduce_sum(np.array([0.5 * float(np.dot(qi, pot))]))[0]
-    return float(u), idx, qi[:, None] * (e_in + e_out), pot
+    u = comm.allreduce_sum(np.array([u_part]))[0]
+    return float(u), idx, forces, pot
 
 
 def shard_update_local(backend, xyz, q, nparts):
     """All parts of the sharded step in one process (stage by stage), for a
-    single device or for tests: the exchanges become plain sums."""
-    q_host = np.asarray(q.cpu().numpy() if hasattr(q, "cpu") else q, dtype=np.float64)
+    single device or for tests: the two all-reduces become sums over the
+    parts' arrays."""
     near = [backend.near(xyz, q, p, nparts) for p in range(nparts)]
     phi_mon = np.sum([r[3] for r in near], axis=0)
-    n = q_host.shape[0]
+    n = len(q)
     forces = np.zeros((n, 3))
     pot = np.zeros(n)
-    u = 0.0
+    u_parts = []
     seen = np.zeros(n, dtype=np.int64)
     for p in range(nparts):
         idx, phi_in, e_in, _ = near[p]
-        idx2, phi_out, e_out = backend.far(xyz, q, phi_mon, p, nparts)
+        idx2, pot_p, f_p, u_p = backend.far(xyz, q, phi_mon, phi_in, e_in, p, nparts)
         if not np.array_equal(idx, idx2):
             raise RuntimeError("near and far stages disagree on the owned particles")
-        pot[idx] = phi_in + phi_out
-        forces[idx] = q_host[idx, None] * (e_in + e_out)
-        u += 0.5 * float(np.dot(q_host[idx], pot[idx]))
+        pot[idx] = pot_p
+        forces[idx] = f_p
+        u_parts.append(u_p)
         seen[idx] += 1
     if not np.all(seen == 1):
         raise RuntimeError("the parts do not cover every particle exactly once")
-    return u, forces, pot
+    return float(np.sum(u_parts)), forces, pot

@@ -114,7 +114,8 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
     assert lib.hsma_energy_forces_batched(None, 2, off, ctypes.byref(parts), e, None, None, None) == ARG
     cnt = ctypes.c_int64()
     assert lib.hsma_shard_near(None, ctypes.byref(parts), 0, 1, None, None, None, ctypes.byref(cnt), None) == ARG
-    assert lib.hsma_shard_far(None, ctypes.byref(parts), None, 0, 1, None, None, None, ctypes.byref(cnt)) == ARG
+    assert lib.hsma_shard_far(None, ctypes.byref(parts), None, None, None, 0, 0, 1, None, None, None, ctypes.byref(cnt),
+                              None) == ARG
     tun = hsma.hsma_tuning(14, 48, 0.0)
     assert lib.hsma_plan_set_tuning(None, ctypes.byref(tun)) == ARG
     assert lib.hsma_plan_get_tuning(None, 2, off, ctypes.byref(tun)) == ARG

@@ -189,7 +189,7 @@ def test_ragged_sizes_fp64(n):
 
 def test_tensor_core_fit_matches_fp64_fit(small_periodic, grounded_small):
     """The fit on the tensor cores (split-BF16 products, FP32 accumulation in
-    tensor memory, one FP64-residual refinement) against the FP64 fit of the
+    tensor memory, one refinement with a compensated residual) against the FP64 fit of the
     same monitoring potentials: the FP32 and tensor-core forms share the pair
     kernel, so b is identical and A differs only by the fit's arithmetic.
     Each operand is held to ~1e-5 relative by its two BF16 words; the
@@ -223,6 +223,44 @@ def test_tensor_core_fit_matches_fp64_fit(small_periodic, grounded_small):
             assert np.all(st == 0)
     for i in range(len(systems)):
         assert rel_energy_err(E["fp32_tc"][i], E["fp32"][i], systems[i][1]) <= 5e-7, i
+
+
+def _tc_batch_against_fp64_fit(w, sizes, seed):
+    """Energies of a batch with the tensor-core fit against the same batch
+    with the FP64 fit (same pair sums, so only the fit differs)."""
+    systems = [I.uniform_pm1(int(n), w.box, seed_offset=seed + i) for i, n in enumerate(sizes)]
+    xyz = np.concatenate([a for a, _ in systems])
+    q = np.concatenate([b for _, b in systems])
+    off = np.concatenate([[0], np.cumsum([len(b) for _, b in systems])])
+    E = {}
+    for prec in ("fp32", "fp32_tc"):
+        with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=prec) as plan:
+            E[prec], _, _, st = plan.energy_forces_batched(*to_dev(xyz, q), off)
+            assert np.all(st == 0)
+    return [rel_energy_err(E["fp32_tc"][i], E["fp32"][i], systems[i][1]) for i in range(len(systems))]
+
+
+def test_tensor_core_fit_many_systems():
+    """More than eight systems: the refinement residual takes its
+    many-systems form (a lane per system, blocks of 32 systems); 40 systems
+    span two such blocks."""
+    errs = _tc_batch_against_fp64_fit(I.SMALL_PERIODIC, [150 + 37 * i for i in range(40)], 720)
+    assert max(errs) <= 5e-7, errs
+
+
+def test_tensor_core_fit_above_the_shared_memory_form():
+    """At p = 34 (1224 fitted columns) the residual's operands no longer fit
+    in shared memory and are read from global memory instead; both the
+    few-systems (3 systems) and the many-systems (12) forms.  alpha = 1.5:
+    at alpha = 2 and this order the reduced-precision path as a whole (FP32
+    pair sums with an FP64 fit) already leaves ~4e-5 of the FP64 energy,
+    because the fit maps rounding in b onto the high-order coefficients
+    amplified by about alpha^P (Sec. II.A error estimate)."""
+    P = 34
+    w = I.Workload("periodic-p34", (1.0, 1.0, 1.0), I.PERIODIC, P, 1.5 * 0.5 * 3.0 ** 0.5, 6000, 1400)
+    for sizes in ([300, 500, 400], [200 + 20 * i for i in range(12)]):
+        errs = _tc_batch_against_fp64_fit(w, sizes, 760)
+        assert max(errs) <= 1e-6, errs
 
 
 def test_tensor_core_fit_high_order():

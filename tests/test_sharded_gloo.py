@@ -47,7 +47,7 @@ class OracleBackend:
         phi_mon[mlo:mhi] = oracle.coulomb(s_xyz, s_q, self.mon[mlo:mhi], field=False)
         return idx, phi, fld, phi_mon
 
-    def far(self, xyz, q, phi_mon, part, nparts):
+    def far(self, xyz, q, phi_mon, phi_in, e_in, part, nparts):
         import oracle
         oh = self.oh
         n = len(q)
@@ -59,7 +59,9 @@ class OracleBackend:
         img_xyz, img_q, _, _ = oh.surface_images(self.plan, A)
         idx = np.arange(part * n // nparts, (part + 1) * n // nparts)
         phi, fld = oracle.coulomb(img_xyz, img_q, c[idx], field=True)
-        return idx, phi, fld
+        qi = np.asarray(q, dtype=np.float64)[idx]
+        pot = phi_in + phi
+        return idx, pot, qi[:, None] * (e_in + fld), 0.5 * float(np.dot(qi, pot))
 
 
 WORKLOAD = I.Workload("sharded-test", (1.0, 1.0, 1.0), I.PERIODIC, 6, 1.5, 600, 200)
@@ -124,7 +126,7 @@ class _DyingBackend:
     def near(self, xyz, q, part, nparts):
         raise RuntimeError("injected failure in the near-field stage")
 
-    def far(self, xyz, q, phi_mon, part, nparts):
+    def far(self, xyz, q, phi_mon, phi_in, e_in, part, nparts):
         raise AssertionError("not reached")
 
 

@@ -52,17 +52,17 @@ def _built():
 
 @pytest.mark.parametrize("prec", [1, 0])
 def test_static_entry_point_matches_allocating_one_twice(prec):
-    import torch
+    from paper_1806_04801_gb300 import hsma
     for call, (ns, nt, seed) in enumerate([(60000, 4000, 11), (7001, 1333, 12)]):
         src, tgt = _inputs(ns, nt, seed + 10 * prec)
-        free_before = torch.cuda.mem_get_info()[0]
+        allocs_before = hsma.allocation_calls()
         rc, pot, fld = _abi_call("hsma_coulomb_sum_static", src, tgt, prec)
-        free_after = torch.cuda.mem_get_info()[0]
         assert rc == 0, f"call {call}: code {rc}"
-        if call == 1:
-            assert free_after == free_before  # nothing allocated by the second call
+        # the library made no allocation or free call during this call
+        assert hsma.allocation_calls() == allocs_before
         rc2, pot_ref, fld_ref = _abi_call("hsma_coulomb_sum", src, tgt, prec)
         assert rc2 == 0
+        assert hsma.allocation_calls() > allocs_before  # the counter sees the allocating entry point's calls
         assert np.all(np.isfinite(pot)) and np.all(np.isfinite(fld))
         assert _rms(pot - pot_ref) <= TOL[prec] * _rms(pot_ref), (call, _rms(pot - pot_ref) / _rms(pot_ref))
         assert _rms(fld - fld_ref) <= 10 * TOL[prec] * _rms(fld_ref)
@@ -71,6 +71,8 @@ def test_static_entry_point_matches_allocating_one_twice(prec):
 def test_static_entry_point_rejects_calls_beyond_its_array():
     from paper_1806_04801_gb300 import hsma
     src, tgt = _inputs(1_200_000, 100, 5)  # 38 MB of source records > 32 MiB
+    allocs_before = hsma.allocation_calls()
     rc, pot, _ = _abi_call("hsma_coulomb_sum_static", src, tgt, 1)
     assert rc == -11 and "memory budget" in hsma.strerror(rc)
+    assert hsma.allocation_calls() == allocs_before
     assert np.all(np.isnan(pot))  # no work was done

@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving summaries")
     ap.add_argument("--workload", default="periodic",
-                    choices=["periodic", "batched", "serving", "grounded", "basis", "paper"])
+                    choices=["periodic", "batched", "serving", "grounded", "basis", "paper", "md"])
     ap.add_argument("--basis-points", type=int, default=4_000_000, help="points of the basis workload")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests in the Poisson trace")
     ap.add_argument("--tuning", default=None,
@@ -173,6 +173,58 @@ def run_series_far_field(dx, dq, w, precision: str, tuning: dict, images_ms: flo
             best = t if best is None or t[7] < best[7] else best
     return {"far_field_ms": best[5], "step_ms": best[7], "images_far_field_ms": images_ms,
             "energy": U, "rel_energy_diff_vs_images": abs(U - U_images) / abs(U_images)}
+
+
+def run_md(steps: int = 20, sizes=(4000, 100_000), precision: str = "fp32_tc"):
+    """Repeated update steps of one moving system, as in molecular dynamics
+    (the paper's application, Sec. III and IV): ms per step with the in-set
+    rebuilt every step (skin 0) and with the in-set reused between steps
+    (hsma_plan_set_inset_skin), and the cost of a step that builds the
+    reusable list.  The particles drift along fixed random directions, at
+    most 0.9 skin over the run (no rebuild is due)."""
+    import torch
+    from paper_1806_04801_gb300 import hsma
+    from paper_1806_04801_gb300 import inputs as I
+    w = I.LARGE_PERIODIC
+    skin = 0.02
+    out = []
+    for n in sizes:
+        xyz, q = I.large_periodic(n)
+        g = np.random.default_rng(9)
+        u = g.standard_normal((n, 3))
+        u *= (0.9 * skin / steps) / np.linalg.norm(u, axis=1, keepdims=True)
+        x0 = torch.as_tensor(xyz).cuda()
+        du = torch.as_tensor(u).cuda()
+        dq = torch.as_tensor(q).cuda()
+        row = {"N": n, "steps": steps, "skin": skin}
+        with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision=precision) as plan:
+            for label, sk in (("rebuild_every_step", 0.0), ("reuse", skin)):
+                plan.set_inset_skin(sk)
+                plan.energy_forces(x0, dq)          # builds the list (reuse) / warms the graph
+                plan.energy_forces(torch.remainder(x0 + 0.5 * du, 1.0), dq)
+                times = []
+                for t in range(steps):
+                    xt = torch.remainder(x0 + t * du, 1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    plan.energy_forces(xt, dq)
+                    e1.record()
+                    e1.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                row[label + "_ms"] = float(np.median(times))
+            # a step that builds the list: the first one after the skin is set again
+            plan.set_inset_skin(skin)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.energy_forces(x0, dq)
+            e1.record()
+            e1.synchronize()
+            row["build_step_ms"] = e0.elapsed_time(e1)
+            row["inset_stats"] = plan.inset_stats()
+        row["speedup_reuse"] = row["rebuild_every_step_ms"] / row["reuse_ms"]
+        out.append(row)
+    return {"workload": "md-periodic-p12 (N charges drifting < 0.9 skin, fp32_tc)", "precision": precision,
+            "rows": out}
 
 
 def fixed_tuning(args):
@@ -568,6 +620,14 @@ def main():
                         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                         "data": "synthetic", "config": {"workload": r["workload"]}, "detail": r}
+            elif args.workload == "md":
+                r = run_md(max(args.steps, 10))
+                big = r["rows"][-1]
+                line = {"metric": "ms per MD step (in-set reuse vs rebuild)", "value": 1000.0 / big["reuse_ms"],
+                        "unit": "systems/s", "n_gpus": 1, "steps": args.steps, "warmup": 2,
+                        "ms_per_step": big["reuse_ms"], "higher_is_better": True, "scaling": "weak",
+                        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                        "config": {"workload": r["workload"]}, "detail": r}
             elif args.workload == "grounded":
                 r = run_grounded(args.steps, args.warmup)
                 line = {"metric": METRIC, "value": r["systems_per_s"], "unit": "systems/s", "n_gpus": 1,
@@ -713,6 +773,7 @@ def main():
         extras = {"batched": side(batched)}
         extras["serving"] = side(lambda: run_serving(args.requests))
         extras["paper_config"] = side(lambda: run_paper_config(max(3, min(args.steps, 5)), 2, args.precision))
+        extras["md"] = side(lambda: run_md(10))
         extras["series_far_field"] = side(lambda: run_series_far_field(
             dx, dq, w, args.precision, tuning, phases[5], float(plan.energy_forces(dx, dq)[0])))
 

@@ -153,6 +153,32 @@ int hsma_plan_set_stream(hsma_plan_t plan, void *stream);
 /* Change the arithmetic of later update steps (hsma_precision). */
 int hsma_plan_set_precision(hsma_plan_t plan, int precision);
 
+/* In-set reuse for repeated steps of one moving system (molecular dynamics;
+ * the paper's stated application, Sec. III timing study and Sec. IV).  With
+ * skin > 0, a single-system update step also records the candidate images
+ * within Rs + skin of the sphere's centre (over the image shifts that sphere
+ * needs), the particles' spatial order and their positions.  Later calls
+ * with the same n and precision skip the sort and the in-set generation: one
+ * kernel places every candidate at its particle's current position (a
+ * particle that crossed a periodic wall keeps its unwrapped position: its
+ * images are the same points) and gives the candidates outside Rs charge 0,
+ * so the near-field sums still run over exactly the images inside Rs (Sec.
+ * II.A).  This holds while every particle is within the skin of its recorded
+ * position: an image moves as its particle does, so one that was farther
+ * than Rs + skin from the centre is still outside Rs.  A call where some
+ * particle has moved by the skin or more, or a charge changed, is detected on
+ * the device and redone with a new list (hsma_plan_inset_stats counts such
+ * calls).  Results equal those of a fresh in-set up to the order of the
+ * floating-point sums.  skin = 0 (the default) switches reuse off.  Requires
+ * skin < Rs - R0 and 2 skin < min L_a; else HSMA_E_ARG.  Costs device
+ * memory for n x (shifts of Rs + skin) candidate entries. */
+int hsma_plan_set_inset_skin(hsma_plan_t plan, double skin);
+
+/* Counts of the plan's single-system steps since creation: in-set lists
+ * built, steps that reused a list, and steps redone because the list was
+ * stale.  Any pointer may be NULL. */
+int hsma_plan_inset_stats(hsma_plan_t plan, int64_t *builds, int64_t *reuses, int64_t *stale);
+
 /* Device bytes the plan's workspace needs for a system of n particles
  * (for admission control).  *bytes is an upper bound. */
 int hsma_plan_footprint(hsma_plan_t plan, int64_t n, size_t *bytes);

@@ -73,6 +73,9 @@ def _declare(L):
     L.hsmo_ewald.restype = None
     L.hsmo_ewald.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
                              ctypes.c_int, _dp, _dp]
+    L.hsmo_ewald_cells.restype = ctypes.c_double
+    L.hsmo_ewald_cells.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_long, _lp, _dp, _dp]
     L.hsmo_ewald_sf.restype = None
     L.hsmo_ewald_sf.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double, ctypes.c_int,
                                 ctypes.c_int, _dp, _dp]
@@ -193,6 +196,41 @@ def ewald(xyz, q, L, beta: float, nreal: int, kmax: int):
     lib().hsmo_ewald(n, _ptr(xyz), _ptr(q), _ptr(L), float(beta), int(nreal), int(kmax),
                      _ptr(pot), _ptr(fld))
     return pot, fld
+
+
+def ewald_cells(xyz, q, L, pick=None, tol: float = 1e-12, nthreads: int | None = None, energy: bool = True):
+    """Ewald sum of a large neutral periodic system (tinfoil) with a cell list
+    for the real-space pairs and structure factors for the reciprocal part:
+    the energy, and the potentials (self term removed) and fields at the
+    particles ``pick``.  The splitting beta and the cutoffs follow from tol:
+    erfc(beta rc) and exp(-kcut^2 / 4 beta^2) are both about tol.  With
+    energy=False only the picked particles are evaluated (real space for
+    them alone; rc = L/3, the largest the cell lists allow, which keeps the
+    reciprocal part small) and the energy is None.  Otherwise rc = L/3 up to
+    20000 charges and L/4 beyond (four cells per axis: fewer real-space
+    pairs, more k vectors).
+    Returns (energy, pot[pick], field[pick])."""
+    import math
+    xyz = _d(xyz).reshape(-1, 3)
+    q = _d(q)
+    L = _d(L)
+    n = xyz.shape[0]
+    pick = np.asarray([] if pick is None else pick, dtype=np.int64)
+    x = math.sqrt(-math.log(tol))          # beta rc
+    kx = 2.0 * math.sqrt(-math.log(tol))   # kcut / beta
+    lmin = float(L.min())
+    # cells of rc: with three per axis every pair is visited; four halve that
+    rc = 0.333 * lmin if (not energy or n <= 20000) else 0.25 * lmin
+    beta = x / rc
+    kcut = kx * beta
+    pot = np.empty(len(pick))
+    fld = np.empty((len(pick), 3))
+    th = int(nthreads or os.cpu_count() or 1)
+    e = lib().hsmo_ewald_cells(n, _ptr(xyz), _ptr(q), _ptr(L), beta, rc, kcut, th, 1 if energy else 0, len(pick),
+                               _ptr(pick, _lp), _ptr(pot), _ptr(fld))
+    if not np.isfinite(e):
+        raise ValueError("box too small for the cell lists")
+    return (float(e) if energy else None), pot, fld
 
 
 def ewald_sf(xyz, q, L, beta: float, nreal: int, kmax: int):

@@ -503,3 +503,287 @@ void hsmo_ewald_sf(long n, const double *xyz, const double *q, const double L[3]
     free(c);
     free(s);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Ewald sum for large periodic systems (tinfoil, neutral): the real-space    */
+/* part over pairs closer than rc (minimum image; rc < L_a / 2, cell lists    */
+/* of at least 3 cells per axis), the reciprocal part over |k| <= kcut        */
+/* through structure factors S(k) = sum_j q_j exp(i k.r_j), the self term     */
+/* -beta q_i / sqrt(pi).  Returns the energy                                  */
+/*   U = 1/2 sum_i sum_(j,n)' q_i q_j erfc(beta r)/r                           */
+/*     + (2 pi / V) sum_(k != 0) exp(-k^2 / 4 beta^2) / k^2 |S(k)|^2          */
+/*     - beta / sqrt(pi) sum_i q_i^2,                                         */
+/* and the potential (self term removed) and field at the npick particles    */
+/* pick[] (want_energy = 0: only these; the real-space energy, O(N^2 rc^3), */
+/* is skipped and 0 returned).  A check of the large-N study of Sec. III,    */
+/* independent of HSMA.                                                      */
+/* Threads split the particles; their partial sums are added in thread order  */
+/* (deterministic for a given thread count).                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    long n, i0, i1;
+    const double *xyz, *q;
+    double L[3], beta, rc;
+    int nc[3];
+    const long *head, *next;
+    int M[3];
+    double kcut;
+    double *Sre, *Sim; /* this thread's partial structure factors, (2M+1)^3 */
+    double ureal;
+    int want_energy;   /* 0: skip the real-space energy (picked particles only) */
+} ewc_job;
+
+static long ewc_cell(const double *p, const double L[3], const int nc[3])
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = p[a] / L[a];
+        f -= floor(f);
+        int k = (int)(f * nc[a]);
+        c[a] = k >= nc[a] ? nc[a] - 1 : k;
+    }
+    return ((long)c[0] * nc[1] + c[1]) * nc[2] + c[2];
+}
+
+/* real-space potential and field at point p (excluding particle `self`) */
+static void ewc_real_at(const ewc_job *J, const double *p, long self, double *phi, double *e)
+{
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        double f = p[a] / J->L[a];
+        f -= floor(f);
+        int k = (int)(f * J->nc[a]);
+        c[a] = k >= J->nc[a] ? J->nc[a] - 1 : k;
+    }
+    double ph = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    const double rc2 = J->rc * J->rc, b = J->beta, tsp = 2.0 * J->beta / sqrt(M_PI);
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int cc[3] = {(c[0] + dx + J->nc[0]) % J->nc[0], (c[1] + dy + J->nc[1]) % J->nc[1],
+                             (c[2] + dz + J->nc[2]) % J->nc[2]};
+                long cell = ((long)cc[0] * J->nc[1] + cc[1]) * J->nc[2] + cc[2];
+                for (long j = J->head[cell]; j >= 0; j = J->next[j]) {
+                    if (j == self) continue;
+                    double d[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double v = p[a] - J->xyz[3 * j + a];
+                        v -= J->L[a] * floor(v / J->L[a] + 0.5); /* minimum image */
+                        d[a] = v;
+                    }
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 >= rc2) continue;
+                    double r = sqrt(r2);
+                    double ec = erfc(b * r);
+                    ph += J->q[j] * ec / r;
+                    if (e) {
+                        double g = J->q[j] * (ec + tsp * r * exp(-b * b * r2)) / (r2 * r);
+                        ex += g * d[0];
+                        ey += g * d[1];
+                        ez += g * d[2];
+                    }
+                }
+            }
+    *phi = ph;
+    if (e) {
+        e[0] = ex;
+        e[1] = ey;
+        e[2] = ez;
+    }
+}
+
+/* Each thread: the real-space energy of its particles, and their partial   */
+/* structure factors, particles taken in blocks of EWC_B so that S(k) is     */
+/* traversed once per block.                                                 */
+#define EWC_B 128
+static void *ewc_worker(void *arg)
+{
+    ewc_job *J = (ewc_job *)arg;
+    const int Mx = J->M[0], My = J->M[1], Mz = J->M[2];
+    const int wx = 2 * Mx + 1, wy = 2 * My + 1, wz = 2 * Mz + 1;
+    const long sy = wz, sx = (long)wy * sy;
+    /* per block: cos/sin of 2 pi m x_a / L_a, [m][particle] */
+    double *cx = (double *)malloc(sizeof(double) * wx * EWC_B), *sxn = (double *)malloc(sizeof(double) * wx * EWC_B);
+    double *cy = (double *)malloc(sizeof(double) * wy * EWC_B), *syn = (double *)malloc(sizeof(double) * wy * EWC_B);
+    double *cz = (double *)malloc(sizeof(double) * wz * EWC_B), *szn = (double *)malloc(sizeof(double) * wz * EWC_B);
+    double pr[EWC_B], pim[EWC_B];
+    const double kc2 = J->kcut * J->kcut;
+    double ureal = 0.0;
+    for (long b0 = J->i0; b0 < J->i1; b0 += EWC_B) {
+        const int nb = (int)(J->i1 - b0 < EWC_B ? J->i1 - b0 : EWC_B);
+        for (int u = 0; u < nb; ++u) {
+            const long i = b0 + u;
+            const double *p = J->xyz + 3 * i;
+            if (J->want_energy) {
+                double phi;
+                ewc_real_at(J, p, i, &phi, NULL);
+                ureal += J->q[i] * phi;
+            }
+            for (int m = -Mx; m <= Mx; ++m) {
+                double t = 2.0 * M_PI * m * p[0] / J->L[0];
+                cx[(m + Mx) * EWC_B + u] = cos(t);
+                sxn[(m + Mx) * EWC_B + u] = sin(t);
+            }
+            for (int m = -My; m <= My; ++m) {
+                double t = 2.0 * M_PI * m * p[1] / J->L[1];
+                cy[(m + My) * EWC_B + u] = cos(t);
+                syn[(m + My) * EWC_B + u] = sin(t);
+            }
+            for (int m = -Mz; m <= Mz; ++m) {
+                double t = 2.0 * M_PI * m * p[2] / J->L[2];
+                cz[(m + Mz) * EWC_B + u] = cos(t);
+                szn[(m + Mz) * EWC_B + u] = sin(t);
+            }
+        }
+        for (int mx = -Mx; mx <= Mx; ++mx) {
+            double kx = 2.0 * M_PI * mx / J->L[0];
+            if (kx * kx > kc2) continue;
+            for (int my = -My; my <= My; ++my) {
+                double ky = 2.0 * M_PI * my / J->L[1];
+                double rem = kc2 - kx * kx - ky * ky;
+                if (rem < 0.0) continue;
+                int mz1 = (int)floor(sqrt(rem) * J->L[2] / (2.0 * M_PI));
+                if (mz1 > Mz) mz1 = Mz;
+                const double *ax = cx + (mx + Mx) * EWC_B, *bx = sxn + (mx + Mx) * EWC_B;
+                const double *ay = cy + (my + My) * EWC_B, *by = syn + (my + My) * EWC_B;
+                for (int u = 0; u < nb; ++u) {
+                    const double qi = J->q[b0 + u];
+                    pr[u] = qi * (ax[u] * ay[u] - bx[u] * by[u]);
+                    pim[u] = qi * (ax[u] * by[u] + bx[u] * ay[u]);
+                }
+                const long base = (long)(mx + Mx) * sx + (long)(my + My) * sy + Mz;
+                for (int mz = -mz1; mz <= mz1; ++mz) {
+                    const double *c = cz + (mz + Mz) * EWC_B, *sn = szn + (mz + Mz) * EWC_B;
+                    double re = 0.0, im = 0.0;
+                    for (int u = 0; u < nb; ++u) {
+                        re += pr[u] * c[u] - pim[u] * sn[u];
+                        im += pr[u] * sn[u] + pim[u] * c[u];
+                    }
+                    J->Sre[base + mz] += re;
+                    J->Sim[base + mz] += im;
+                }
+            }
+        }
+    }
+    J->ureal = 0.5 * ureal;
+    free(cx);
+    free(sxn);
+    free(cy);
+    free(syn);
+    free(cz);
+    free(szn);
+    return NULL;
+}
+
+double hsmo_ewald_cells(long n, const double *xyz, const double *q, const double L[3], double beta, double rc,
+                        double kcut, int nthreads, int want_energy, long npick, const long *pick, double *pick_pot,
+                        double *pick_field)
+{
+    int nc[3], M[3];
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)floor(L[a] / rc);
+        if (nc[a] < 3 || 2.0 * rc >= L[a]) return NAN; /* cell lists need 3 cells, minimum image rc < L/2 */
+        M[a] = (int)ceil(kcut * L[a] / (2.0 * M_PI));
+    }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (nthreads > n) nthreads = (int)(n > 0 ? n : 1);
+    const long ncell = (long)nc[0] * nc[1] * nc[2];
+    long *head = (long *)malloc(sizeof(long) * ncell), *next = (long *)malloc(sizeof(long) * n);
+    for (long c = 0; c < ncell; ++c) head[c] = -1;
+    for (long j = n - 1; j >= 0; --j) {
+        long c = ewc_cell(xyz + 3 * j, L, nc);
+        next[j] = head[c];
+        head[c] = j;
+    }
+    const long nk = (long)(2 * M[0] + 1) * (2 * M[1] + 1) * (2 * M[2] + 1);
+    ewc_job jobs[256];
+    pthread_t th[256];
+    long per = (n + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        ewc_job *J = &jobs[t];
+        J->n = n;
+        J->i0 = t * per < n ? t * per : n;
+        J->i1 = (t + 1) * per < n ? (t + 1) * per : n;
+        J->xyz = xyz;
+        J->q = q;
+        for (int a = 0; a < 3; ++a) {
+            J->L[a] = L[a];
+            J->nc[a] = nc[a];
+            J->M[a] = M[a];
+        }
+        J->beta = beta;
+        J->rc = rc;
+        J->head = head;
+        J->next = next;
+        J->kcut = kcut;
+        J->Sre = (double *)calloc(nk, sizeof(double));
+        J->Sim = (double *)calloc(nk, sizeof(double));
+        J->ureal = 0.0;
+        J->want_energy = want_energy;
+    }
+    if (nthreads == 1)
+        ewc_worker(&jobs[0]);
+    else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, ewc_worker, &jobs[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    }
+    /* structure factors and real-space energy, added in thread order */
+    double *Sre = jobs[0].Sre, *Sim = jobs[0].Sim;
+    double ureal = jobs[0].ureal;
+    for (int t = 1; t < nthreads; ++t) {
+        for (long k = 0; k < nk; ++k) {
+            Sre[k] += jobs[t].Sre[k];
+            Sim[k] += jobs[t].Sim[k];
+        }
+        ureal += jobs[t].ureal;
+        free(jobs[t].Sre);
+        free(jobs[t].Sim);
+    }
+    const double V = L[0] * L[1] * L[2], kc2 = kcut * kcut;
+    const long sy = 2 * M[2] + 1, sx = (2 * M[1] + 1) * sy;
+    double urec = 0.0, q2 = 0.0;
+    for (int mx = -M[0]; mx <= M[0]; ++mx)
+        for (int my = -M[1]; my <= M[1]; ++my)
+            for (int mz = -M[2]; mz <= M[2]; ++mz) {
+                if (mx == 0 && my == 0 && mz == 0) continue;
+                double k[3] = {2.0 * M_PI * mx / L[0], 2.0 * M_PI * my / L[1], 2.0 * M_PI * mz / L[2]};
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                if (k2 > kc2) continue;
+                long idx = (long)(mx + M[0]) * sx + (long)(my + M[1]) * sy + (mz + M[2]);
+                urec += exp(-k2 / (4.0 * beta * beta)) / k2 * (Sre[idx] * Sre[idx] + Sim[idx] * Sim[idx]);
+            }
+    urec *= 2.0 * M_PI / V;
+    for (long i = 0; i < n; ++i) q2 += q[i] * q[i];
+    const double energy = want_energy ? ureal + urec - beta / sqrt(M_PI) * q2 : 0.0;
+    /* potential and field at the picked particles */
+    for (long s = 0; s < npick; ++s) {
+        long i = pick[s];
+        const double *p = xyz + 3 * i;
+        double phi, e[3];
+        ewc_real_at(&jobs[0], p, i, &phi, e);
+        for (int mx = -M[0]; mx <= M[0]; ++mx)
+            for (int my = -M[1]; my <= M[1]; ++my)
+                for (int mz = -M[2]; mz <= M[2]; ++mz) {
+                    if (mx == 0 && my == 0 && mz == 0) continue;
+                    double k[3] = {2.0 * M_PI * mx / L[0], 2.0 * M_PI * my / L[1], 2.0 * M_PI * mz / L[2]};
+                    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                    if (k2 > kc2) continue;
+                    long idx = (long)(mx + M[0]) * sx + (long)(my + M[1]) * sy + (mz + M[2]);
+                    double f = 4.0 * M_PI / V * exp(-k2 / (4.0 * beta * beta)) / k2;
+                    double arg = k[0] * p[0] + k[1] * p[1] + k[2] * p[2];
+                    double c = cos(arg), sn = sin(arg);
+                    /* sum_j q_j cos(k.(r - r_j)) = Re(e^{ik.r} conj S);  sin form for the field */
+                    phi += f * (c * Sre[idx] + sn * Sim[idx]);
+                    double im = sn * Sre[idx] - c * Sim[idx];
+                    for (int a = 0; a < 3; ++a) e[a] += f * k[a] * im;
+                }
+        pick_pot[s] = phi - 2.0 * beta * q[i] / sqrt(M_PI);
+        for (int a = 0; a < 3; ++a) pick_field[3 * s + a] = e[a];
+    }
+    free(jobs[0].Sre);
+    free(jobs[0].Sim);
+    free(head);
+    free(next);
+    return energy;
+}

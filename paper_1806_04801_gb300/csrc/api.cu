@@ -146,10 +146,32 @@ struct hsma_plan_s {
     bool events_ready = false;
     double last_ms[8] = {};
     bool have_timings = false;
-    // CUDA graph of the update step for the last batch shape
-    cudaGraphExec_t graph_exec = nullptr;
-    std::vector<long long> graph_key;
-    long long graph_kernels = 0;
+    // CUDA graphs of the update step: the last few batch shapes / step modes
+    struct GraphEntry {
+        std::vector<long long> key;
+        cudaGraphExec_t exec = nullptr;
+        long long kernels = 0;
+        long long last_use = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    long long graph_clock = 0;
+    // reusable in-set for repeated single-system steps (molecular dynamics):
+    // a candidate list at Rs + skin over an enlarged shift table, the Morton
+    // order and the centred positions of its build
+    double md_skin = 0.0;
+    bool md_valid = false;
+    long long md_n = 0, md_ncand = 0;
+    int md_prec = -1, md_nshifts = 0;
+    std::vector<int4> md_shift_host;
+    void *md_mem = nullptr;
+    size_t md_cap = 0;
+    int2 *md_cand = nullptr;
+    int *md_perm = nullptr, *md_counts = nullptr, *md_rcounts = nullptr;
+    double4_32a *md_x0 = nullptr, *md_u = nullptr;
+    int4 *md_shifts = nullptr;
+    long long *md_ns = nullptr, *md_ns_host = nullptr;
+    bool md_shifts_dirty = true;
+    long long md_builds = 0, md_reuses = 0, md_stale = 0;
     cudaStream_t priv_stream = nullptr;
     cudaEvent_t order_ev = nullptr;
 };
@@ -432,6 +454,12 @@ std::vector<double> norm_table(int P)
     return v;
 }
 
+void drop_graphs(hsma_plan_s *p)
+{
+    for (auto &e : p->graphs) cudaGraphExecDestroy(e.exec);
+    p->graphs.clear();
+}
+
 void record(hsma_plan_s *p, cudaStream_t st, int i)
 {
     if (p->profile && p->events_ready) cudaEventRecord(p->ev[i], st);
@@ -441,14 +469,48 @@ void record(hsma_plan_s *p, cudaStream_t st, int i)
 // the workspace staging buffers and writes forces/potentials to the staging
 // outputs, so the same sequence can be captured once into a CUDA graph and
 // replayed for every call with the same batch shape.
+// Step modes for repeated single-system calls (in-set reuse, see
+// hsma_plan_set_inset_skin): kFull builds the in-set from scratch; kBuild
+// does the same and also records the candidate list, Morton order and
+// positions; kReuse regenerates the in-set from the list instead of sorting
+// and building.
+enum StepMode { kFull = 0, kBuild = 1, kReuse = 2 };
+
 int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int prec, bool want_f, bool want_p,
-                   cudaStream_t st)
+                   int mode, cudaStream_t st)
 {
     const int nsys = sh.nsys;
     int rc = HSMA_OK;
     HSMA_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(int) * nsys, st));
     HSMA_CUDA_TRY(cudaMemsetAsync(w.ctrl, 0, sizeof(int) * 8, st));
     record(p, st, 0);
+    const int *perm = w.perm;
+    if (mode == kReuse) {
+        RegenArgs r;
+        r.n = sh.sys[0].n;
+        r.cap = sh.cap_total;
+        r.cap_cand = r.n * p->md_nshifts;
+        r.counts = p->md_rcounts;
+        r.u = p->md_u;
+        r.ncand = p->md_ns;
+        r.cand = p->md_cand;
+        r.shifts = p->md_shifts;
+        r.perm = p->md_perm;
+        r.x0 = p->md_x0;
+        r.xyz = w.xyz;
+        r.q = w.q;
+        for (int a = 0; a < 3; ++a) r.g.L[a] = p->L[a];
+        r.g.Rs = p->Rs;
+        r.g.bc = p->bc;
+        r.skin = p->md_skin;
+        r.src_hi = w.src_hi;
+        r.src_lo = w.src_lo;
+        r.src64 = w.src64;
+        r.ns = w.ns;
+        r.status = w.status;
+        if ((rc = launch_inset_regen(r, st))) return rc;
+        perm = p->md_perm;
+    } else {
 
     // spatial order of the particles (Morton, stable radix sort)
     SortArgs sa;
@@ -488,6 +550,24 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     ia.cenf = w.cenf;
     ia.qsums = w.qsums;
     if ((rc = launch_inset(ia, st))) return rc;
+    if (mode == kBuild) {
+        // candidates within Rs + skin over the enlarged shift table, and the
+        // order and positions they refer to
+        InsetArgs ca = ia;
+        ca.g.Rs = p->Rs + p->md_skin;
+        ca.shifts = p->md_shifts;
+        ca.n_shifts = p->md_nshifts;
+        ca.counts = p->md_counts;
+        ca.ns = p->md_ns;
+        ca.src_hi = ca.src_lo = nullptr;
+        ca.src64 = nullptr;
+        ca.cand = p->md_cand;
+        if ((rc = launch_inset_candidates(ca, st))) return rc;
+        const long long n0 = sh.sys[0].n;
+        HSMA_CUDA_TRY(cudaMemcpyAsync(p->md_perm, w.perm, sizeof(int) * n0, cudaMemcpyDeviceToDevice, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(p->md_x0, w.cen, sizeof(double4_32a) * n0, cudaMemcpyDeviceToDevice, st));
+    }
+    }
     const int TB = pair_targets_per_block(prec, sh.variant);
     if (w.boxes && (rc = launch_tile_boxes(w.sys, nsys, sh.max_tiles, w.ns, w.src_hi, TB, w.boxes, st))) return rc;
     record(p, st, 1);
@@ -548,7 +628,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
             return rc;
         record(p, st, 6);
     }
-    if ((rc = launch_finalize(w.sys, nsys, sh.max_n, w.perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
+    if ((rc = launch_finalize(w.sys, nsys, sh.max_n, perm, w.q, w.phi_tgt, w.e_part, w.phi_out, w.e_out,
                               want_f ? w.forces : nullptr, want_p ? w.pot : nullptr, nullptr, w.upart, w.energy,
                               w.status, st)))
         return rc;
@@ -572,6 +652,105 @@ int work_stream(hsma_plan_s *p, cudaStream_t *out)
     HSMA_CUDA_TRY(cudaEventRecord(p->order_ev, (cudaStream_t)0));
     HSMA_CUDA_TRY(cudaStreamWaitEvent(p->priv_stream, p->order_ev, 0));
     *out = p->priv_stream;
+    return HSMA_OK;
+}
+
+// Device memory of the reusable in-set for systems of n particles.
+size_t carve_md(hsma_plan_s *p, long long n, void *base)
+{
+    const long long nblk = (n + kInsetBlock - 1) / kInsetBlock;
+    Carver c(base);
+    p->md_cand = c.take<int2>((size_t)n * p->md_nshifts);
+    p->md_perm = c.take<int>(n);
+    p->md_x0 = c.take<double4_32a>(n);
+    p->md_u = c.take<double4_32a>(n);
+    p->md_counts = c.take<int>((size_t)p->md_nshifts * nblk);
+    p->md_rcounts = c.take<int>((size_t)p->md_nshifts * nblk + 1);  // per block of 256 candidates
+    p->md_shifts = c.take<int4>(p->md_nshifts);
+    p->md_ns = c.take<long long>(1);
+    return align_up(c.off, 256);
+}
+
+int ensure_md(hsma_plan_s *p, long long n)
+{
+    const size_t need = carve_md(p, n, nullptr);
+    if (need > p->md_cap) {
+        if (p->md_mem) {
+            cudaStreamSynchronize(p->stream ? p->stream : p->priv_stream);
+            dev_free(p->md_mem);
+        }
+        p->md_mem = nullptr;
+        p->md_cap = 0;
+        p->md_valid = false;
+        drop_graphs(p);  // the cached graphs hold pointers into the old list
+        HSMA_CUDA_TRY(dev_malloc(&p->md_mem, need));
+        p->md_cap = need;
+        p->md_shifts_dirty = true;
+    }
+    carve_md(p, n, p->md_mem);
+    if (!p->md_ns_host) HSMA_CUDA_TRY(host_malloc(&p->md_ns_host, sizeof(long long)));
+    if (p->md_shifts_dirty) {
+        HSMA_CUDA_TRY(cudaMemcpy(p->md_shifts, p->md_shift_host.data(), sizeof(int4) * p->md_nshifts,
+                                 cudaMemcpyHostToDevice));
+        p->md_shifts_dirty = false;
+    }
+    return HSMA_OK;
+}
+
+// Enqueue one update step in the given mode: by replaying a CUDA graph of
+// it (captured on first use for this batch shape, mode and buffers) or, with
+// graphs off or profiling on, by direct launches.
+int launch_step(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int prec, bool want_f, bool want_p,
+                int mode, const std::vector<long long> &n, cudaStream_t st)
+{
+    if (!(p->use_graphs && !p->profile)) return enqueue_update(p, sh, w, prec, want_f, want_p, mode, st);
+    std::vector<long long> key = {prec,
+                                  sh.nsys,
+                                  want_f,
+                                  want_p,
+                                  (long long)(uintptr_t)p->ws_mem,
+                                  sh.variant,
+                                  (long long)sh.items,
+                                  mode,
+                                  (long long)(uintptr_t)p->md_mem};
+    key.insert(key.end(), n.begin(), n.end());
+    hsma_plan_s::GraphEntry *g = nullptr;
+    for (auto &e : p->graphs)
+        if (e.key == key) g = &e;
+    if (!g) {
+        constexpr size_t kKeep = 3;  // graphs cached per plan
+        if (p->graphs.size() >= kKeep) {
+            auto old = std::min_element(p->graphs.begin(), p->graphs.end(),
+                                        [](const auto &a, const auto &b) { return a.last_use < b.last_use; });
+            cudaGraphExecDestroy(old->exec);
+            p->graphs.erase(old);
+        }
+        long long before = g_launches.load();
+        HSMA_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_update(p, sh, w, prec, want_f, want_p, mode, st);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (rc || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (!rc) set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+            return rc ? rc : HSMA_E_CUDA;
+        }
+        hsma_plan_s::GraphEntry e;
+        ce = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            set_last_cuda_error(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
+            return HSMA_E_CUDA;
+        }
+        e.kernels = g_launches.load() - before;
+        g_launches.fetch_sub(e.kernels);  // counted when replayed
+        e.key = key;
+        p->graphs.push_back(e);
+        g = &p->graphs.back();
+    }
+    g->last_use = ++p->graph_clock;
+    HSMA_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+    g_launches.fetch_add(g->kernels);
     return HSMA_OK;
 }
 
@@ -620,50 +799,42 @@ int run_update(hsma_plan_s *p, int nsys, const int64_t *offsets, const hsma_part
     HSMA_CUDA_TRY(cudaMemcpyAsync(w.q, all->q, sizeof(double) * sh.n_total, in_kind, st));
 
     const bool want_f = forces != nullptr, want_p = pot != nullptr;
-    const bool graphs = p->use_graphs && !p->profile;
-    if (graphs) {
-        std::vector<long long> key = {prec, nsys, want_f, want_p, (long long)(uintptr_t)p->ws_mem, sh.variant,
-                                      (long long)sh.items};
-        key.insert(key.end(), n.begin(), n.end());
-        if (!p->graph_exec || key != p->graph_key) {
-            if (p->graph_exec) {
-                cudaGraphExecDestroy(p->graph_exec);
-                p->graph_exec = nullptr;
-            }
-            long long before = g_launches.load();
-            HSMA_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            rc = enqueue_update(p, sh, w, prec, want_f, want_p, st);
-            cudaGraph_t graph = nullptr;
-            cudaError_t ce = cudaStreamEndCapture(st, &graph);
-            if (rc || ce != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                if (!rc) set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
-                return rc ? rc : HSMA_E_CUDA;
-            }
-            ce = cudaGraphInstantiate(&p->graph_exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ce != cudaSuccess) {
-                set_last_cuda_error(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
-                p->graph_exec = nullptr;
-                return HSMA_E_CUDA;
-            }
-            p->graph_kernels = g_launches.load() - before;
-            g_launches.fetch_sub(p->graph_kernels);  // counted when replayed
-            p->graph_key = key;
-        }
-        HSMA_CUDA_TRY(cudaGraphLaunch(p->graph_exec, st));
-        g_launches.fetch_add(p->graph_kernels);
-    } else {
-        if ((rc = enqueue_update(p, sh, w, prec, want_f, want_p, st))) return rc;
+    int mode = kFull;
+    if (p->md_skin > 0.0 && nsys == 1) {
+        if ((rc = ensure_md(p, n[0]))) return rc;
+        mode = (p->md_valid && p->md_n == n[0] && p->md_prec == prec) ? kReuse : kBuild;
     }
-
-    HSMA_CUDA_TRY(cudaMemcpyAsync(h_energy, w.energy, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
-    HSMA_CUDA_TRY(cudaMemcpyAsync(h_status, w.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
-    HSMA_CUDA_TRY(cudaMemcpyAsync(h_ns, w.ns, sizeof(long long) * nsys, cudaMemcpyDeviceToHost, st));
-    if (want_f) HSMA_CUDA_TRY(cudaMemcpyAsync(forces, w.forces, sizeof(double) * 3 * sh.n_total, out_kind, st));
-    if (want_p) HSMA_CUDA_TRY(cudaMemcpyAsync(pot, w.pot, sizeof(double) * sh.n_total, out_kind, st));
-    HSMA_CUDA_TRY(cudaStreamSynchronize(st));
-    HSMA_CUDA_TRY(cudaGetLastError());
+    auto device_step = [&](int m) -> int {
+        int r = launch_step(p, sh, w, prec, want_f, want_p, m, n, st);
+        if (r) return r;
+        HSMA_CUDA_TRY(cudaMemcpyAsync(h_energy, w.energy, sizeof(double) * nsys, cudaMemcpyDeviceToHost, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(h_status, w.status, sizeof(int) * nsys, cudaMemcpyDeviceToHost, st));
+        HSMA_CUDA_TRY(cudaMemcpyAsync(h_ns, w.ns, sizeof(long long) * nsys, cudaMemcpyDeviceToHost, st));
+        if (m == kBuild)
+            HSMA_CUDA_TRY(cudaMemcpyAsync(p->md_ns_host, p->md_ns, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        if (want_f) HSMA_CUDA_TRY(cudaMemcpyAsync(forces, w.forces, sizeof(double) * 3 * sh.n_total, out_kind, st));
+        if (want_p) HSMA_CUDA_TRY(cudaMemcpyAsync(pot, w.pot, sizeof(double) * sh.n_total, out_kind, st));
+        HSMA_CUDA_TRY(cudaStreamSynchronize(st));
+        HSMA_CUDA_TRY(cudaGetLastError());
+        return HSMA_OK;
+    };
+    if ((rc = device_step(mode))) return rc;
+    if (mode == kReuse && (h_status[0] & ST_STALE)) {
+        // a particle moved by the skin or more (or the charges changed): the
+        // list no longer covers the in-set; redo the step with a new list
+        ++p->md_stale;
+        p->md_valid = false;
+        mode = kBuild;
+        if ((rc = device_step(mode))) return rc;
+    }
+    if (mode == kReuse) ++p->md_reuses;
+    if (mode == kBuild) {
+        ++p->md_builds;
+        p->md_valid = map_status(h_status[0]) == HSMA_OK;
+        p->md_n = n[0];
+        p->md_ncand = *p->md_ns_host;
+        p->md_prec = prec;
+    }
 
     if (p->profile && p->events_ready) {
         const int from[8] = {0, 1, 2, 3, 4, 5, 6, 0};
@@ -995,11 +1166,7 @@ void hsma::plan_trim_workspace(hsma_plan_t p, size_t max_keep)
     if (!p || p->ws_cap <= max_keep || !p->ws_mem) return;
     cudaStream_t st = p->stream ? p->stream : p->priv_stream;
     if (st) cudaStreamSynchronize(st);
-    if (p->graph_exec) {
-        cudaGraphExecDestroy(p->graph_exec);
-        p->graph_exec = nullptr;
-        p->graph_key.clear();
-    }
+    drop_graphs(p);
     dev_free(p->ws_mem);
     p->ws_mem = nullptr;
     p->ws_cap = 0;
@@ -1230,7 +1397,9 @@ void hsma_plan_destroy(hsma_plan_t pl)
     if (!pl) return;
     if (pl->stream || pl->ws_mem || pl->plan_mem) cudaStreamSynchronize(pl->stream);
     if (pl->priv_stream) cudaStreamSynchronize(pl->priv_stream);
-    if (pl->graph_exec) cudaGraphExecDestroy(pl->graph_exec);
+    drop_graphs(pl);
+    if (pl->md_mem) dev_free(pl->md_mem);
+    if (pl->md_ns_host) host_free(pl->md_ns_host);
     if (pl->priv_stream) cudaStreamDestroy(pl->priv_stream);
     if (pl->order_ev) cudaEventDestroy(pl->order_ev);
     if (pl->events_ready)
@@ -1301,6 +1470,58 @@ int hsma_plan_set_precision(hsma_plan_t pl, int precision)
 {
     if (!pl || precision < 0 || precision > 2) return HSMA_E_ARG;
     pl->precision = precision;
+    return HSMA_OK;
+}
+
+int hsma_plan_set_inset_skin(hsma_plan_t pl, double skin)
+{
+    if (!pl || !(skin >= 0.0)) return HSMA_E_ARG;
+    const double lmin = std::min(pl->L[0], std::min(pl->L[1], pl->L[2]));
+    // a particle displaced by less than the skin must stay inside the sphere
+    // (Rs - R0 is the margin of the box's corners) and within half a box of
+    // its build position (the minimum image of the displacement)
+    if (skin > 0.0 && !(skin < pl->Rs - pl->R0 && 2.0 * skin < lmin)) return HSMA_E_ARG;
+    if (skin > 0.0) {
+        // shells of the candidates' sphere Rs + skin
+        int K[3];
+        long long nsh = 1;
+        for (int a = 0; a < 3; ++a) {
+            K[a] = shells(pl->Rs + skin, pl->L[a]);
+            nsh *= 2LL * K[a] + 1;
+        }
+        if (nsh > kMaxShifts) return HSMA_E_ARG;
+        // the plan's own shifts first, in their order (the in-set of a reused
+        // step then has the order, and the tiles, of a fresh one), then the
+        // shifts only the larger sphere needs
+        std::vector<int4> sh;
+        int Kp[3];
+        for (int a = 0; a < 3; ++a) Kp[a] = shells(pl->Rs, pl->L[a]);
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 0) sh.push_back(make_int4(0, 0, 0, 0));
+            for (int kx = -K[0]; kx <= K[0]; ++kx)
+                for (int ky = -K[1]; ky <= K[1]; ++ky)
+                    for (int kz = -K[2]; kz <= K[2]; ++kz) {
+                        if (!kx && !ky && !kz) continue;
+                        const bool own = abs(kx) <= Kp[0] && abs(ky) <= Kp[1] && abs(kz) <= Kp[2];
+                        if (own == (pass == 0))
+                            sh.push_back(make_int4(kx, ky, kz, (abs(kx) + abs(ky) + abs(kz)) & 1));
+                    }
+        }
+        pl->md_shift_host = sh;
+        pl->md_nshifts = (int)sh.size();
+        pl->md_shifts_dirty = true;
+    }
+    pl->md_skin = skin;
+    pl->md_valid = false;
+    return HSMA_OK;
+}
+
+int hsma_plan_inset_stats(hsma_plan_t pl, int64_t *builds, int64_t *reuses, int64_t *stale)
+{
+    if (!pl) return HSMA_E_ARG;
+    if (builds) *builds = pl->md_builds;
+    if (reuses) *reuses = pl->md_reuses;
+    if (stale) *stale = pl->md_stale;
     return HSMA_OK;
 }
 

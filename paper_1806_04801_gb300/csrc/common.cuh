@@ -61,6 +61,7 @@ enum : int {
     ST_COINCIDENT = 4,
     ST_TIMEOUT = 8,
     ST_CAPACITY = 16,
+    ST_STALE = 32,  // reused in-set no longer valid (a particle moved >= the skin, or charges changed)
 };
 
 // ------------------------------------------------------------ batch layout
@@ -337,8 +338,38 @@ struct InsetArgs {
     double4_32a *cen;       // [n] scratch: centred (x, y, z, q) in spatial order
     float4 *cenf;           // [n] the same rounded to FP32 (the guarded in-sphere test)
     double2 *qsums;         // [blocks] per particle block: (sum q, sum |q|)
+    int2 *cand = nullptr;   // candidate pass only: (spatial index, shift) of each hit
 };
 int launch_inset(const InsetArgs &a, cudaStream_t st);
+// The candidate list of a reusable in-set: the same count/scan/scatter over
+// a's shifts and radius (the caller passes the enlarged sphere and shift
+// table, its own counts / ns buffers and a.cand), after launch_inset of the
+// same step has filled cen / cenf.
+int launch_inset_candidates(const InsetArgs &a, cudaStream_t st);
+
+// In-set regenerated from a candidate list (single system): image positions
+// from the particles' current positions, continued without wrapping from the
+// positions of the list's build; the candidates inside Rs, compacted in
+// list order (inset.cu).
+struct RegenArgs {
+    long long n, cap;        // particles; in-set slots of the workspace
+    long long cap_cand;      // candidate list capacity
+    const long long *ncand;  // device: candidates in the list
+    const int2 *cand;        // (spatial index, shift index)
+    const int4 *shifts;
+    const int *perm;         // spatial index -> caller index (of the build)
+    const double4_32a *x0;   // centred positions and charges at the build, spatial order
+    const double *xyz, *q;   // current positions (box frame) and charges, caller order
+    Geometry g;              // the sphere Rs of the step
+    double skin;             // a particle displaced by >= skin makes the list stale
+    int *counts;             // [candidate blocks] scratch
+    double4_32a *u;          // [n] scratch: continued positions and charges, spatial order
+    float4 *src_hi, *src_lo;
+    double4_32a *src64;
+    long long *ns;
+    int *status;
+};
+int launch_inset_regen(const RegenArgs &r, cudaStream_t st);
 
 // pair.cu
 struct PairArgs {

@@ -88,6 +88,8 @@ SIGNATURES = {
     "hsma_version": (ctypes.c_char_p, []),
     "hsma_kernel_launches": (_I64, []),
     "hsma_allocation_calls": (_I64, []),
+    "hsma_plan_set_inset_skin": (_I, [_VP, _D]),
+    "hsma_plan_inset_stats": (_I, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "hsma_fp32_peak": (_I, [_VP, _VP]),
     "hsma_last_timings": (_I, [_VP, _VP, _I]),
     "hsma_last_get": (_I64, [_VP, _I, _VP, _I64]),
@@ -369,6 +371,21 @@ class Plan:
         if rc != HSMA_OK:
             raise HsmaError(rc, "hsma_energy_forces_batched", status=st)
         return e, f, p, st
+
+    # ------------------------------------------------------ in-set reuse
+    def set_inset_skin(self, skin: float):
+        """hsma_plan_set_inset_skin: reuse the in-set between single-system
+        steps while every particle stays within ``skin`` of the positions of
+        the last build (0 switches reuse off)."""
+        _check(_lib().hsma_plan_set_inset_skin(self._h, float(skin)), "hsma_plan_set_inset_skin")
+
+    def inset_stats(self) -> dict:
+        """hsma_plan_inset_stats: in-set lists built, steps that reused one,
+        steps redone because the list was stale."""
+        b, r, st = _I64(), _I64(), _I64()
+        _check(_lib().hsma_plan_inset_stats(self._h, ctypes.byref(b), ctypes.byref(r), ctypes.byref(st)),
+               "hsma_plan_inset_stats")
+        return {"builds": b.value, "reuses": r.value, "stale": st.value}
 
     # ---------------------------------------------------- target sharding
     def _shard_args(self, xyz, q):

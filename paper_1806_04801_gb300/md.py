@@ -7,6 +7,9 @@ the update step's CUDA graph is replayed each step -- and integrates with
 velocity Verlet on device tensors.  Positions stay in the box frame (periodic
 coordinates are wrapped after each drift).  A caller-supplied short-range
 term (e.g. a repulsive core) is added to the electrostatic energy and forces.
+With a skin, the plan reuses its in-set between steps (the sort and the image
+generation run only when some particle has moved by the skin since the last
+build; hsma_plan_set_inset_skin).
 """
 from __future__ import annotations
 
@@ -18,12 +21,16 @@ class VelocityVerlet:
     xyz, q, v:   CUDA float64 tensors (n, 3), (n,), (n, 3)
     mass:        scalar or (n,) tensor
     short_range: optional callable xyz -> (energy, forces) on the same device
+    skin:        if given, the plan's in-set reuse skin (0 switches it off)
     """
 
-    def __init__(self, plan, xyz, q, v, mass, dt: float, box, periodic: bool = True, short_range=None):
+    def __init__(self, plan, xyz, q, v, mass, dt: float, box, periodic: bool = True, short_range=None,
+                 skin=None):
         import torch
         self.torch = torch
         self.plan = plan
+        if skin is not None:
+            plan.set_inset_skin(skin)
         self.x = xyz.clone()
         self.q = q
         self.v = v.clone()

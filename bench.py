@@ -383,24 +383,50 @@ def run_grounded(steps: int, warmup: int):
 
 
 # ------------------------------------------------------- serving workload
-def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, lanes: int = 2, max_batch: int = 32):
+def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, lanes: int = 3, max_batch: int = 32,
+                express_lanes: int = 1, express_max_n: int = 20000):
     """Poisson stream of periodic boxes with N log-uniform in [1000, 200000]:
     requests are submitted at their arrival times to the continuous-batching
-    server; latency is submit -> result."""
+    server; latency is submit -> result.  One express lane (high-priority
+    stream) serves requests of at most express_max_n particles, the bulk
+    lanes the rest with preemptible pair work.  Besides p50/p99 of the
+    latency, each request's slowdown -- its latency over the time the same
+    request takes alone through a plan with host buffers -- is reported:
+    with N spanning 200x the latency percentiles mostly restate the size
+    mix, the slowdown shows the queueing."""
     import threading
     from paper_1806_04801_gb300 import hsma
     from paper_1806_04801_gb300 import inputs as I
     w = I.SERVING_PERIODIC
 
+    # time alone (one request, host buffers) over the size range, for the slowdown
+    sizes_ref = [1000, 3000, 10000, 30000, 100000, 200000]
+    alone = []
+    with hsma.Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32_tc") as pl:
+        for n in sizes_ref:
+            x, q = I.uniform_pm1(n, w.box, seed_offset=9000 + n)
+            pl.energy_forces(x, q)
+            ts = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                pl.energy_forces(x, q)
+                ts.append((time.perf_counter() - t0) * 1000.0)
+            alone.append(min(ts))
+    la, ln = np.log(alone), np.log(sizes_ref)
+
+    def t_alone(n):
+        return float(np.exp(np.interp(np.log(n), ln, la)))
+
     def replay(rate, count, seed):
         t_arr, sizes = I.poisson_trace(count, rate_hz=rate, seed_offset=4 + seed)
         reqs = [I.uniform_pm1(int(n), w.box, seed_offset=5000 + seed * 1000 + i) for i, n in enumerate(sizes)]
         with hsma.Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32_tc", lanes=lanes,
-                         max_batch=max_batch) as srv:
-            # warm the lanes (plans, workspaces)
+                         max_batch=max_batch, express_lanes=express_lanes, express_max_n=express_max_n) as srv:
+            # warm the lanes (plans, workspaces): a small and a large request each
             for _ in range(lanes):
-                tk = srv.submit(*reqs[0])
-                srv.result(tk, n=len(reqs[0][1]), forces=False)
+                for r in (reqs[int(np.argmin(sizes))], reqs[int(np.argmax(sizes))]):
+                    tk = srv.submit(*r)
+                    srv.result(tk, forces=False)
             tickets = [None] * count
             t0 = time.perf_counter()
 
@@ -412,24 +438,32 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
                     tickets[i] = srv.submit(*reqs[i])
             th = threading.Thread(target=feeder)
             th.start()
-            lat, batch = [], []
+            lat, batch, slow, nn = [], [], [], []
             th.join()
             for i in range(count):
-                code, e, _, info = srv.result(tickets[i], n=len(reqs[i][1]), forces=False)
+                code, e, _, info = srv.result(tickets[i], forces=False)
                 if code == 0:
                     lat.append(info["latency_ms"])
                     batch.append(info["batch_size"])
+                    slow.append(info["latency_ms"] / t_alone(len(reqs[i][1])))
+                    nn.append(len(reqs[i][1]))
             wall = time.perf_counter() - t0
             st = srv.stats()
-        lat = np.array(lat)
+        lat, slow, nn = np.array(lat), np.array(slow), np.array(nn)
+        small = nn <= express_max_n
+        pct = lambda a, p: float(np.percentile(a, p)) if len(a) else None  # noqa: E731
         return {"rate_hz": rate, "requests": count, "completed": int(len(lat)),
-                "systems_per_s": len(lat) / wall, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(np.mean(batch)),
-                "wall_s": wall, "hbm_budget_bytes": int(st["hbm_budget_bytes"])}
+                "systems_per_s": len(lat) / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "slowdown_p50": pct(slow, 50), "slowdown_p99": pct(slow, 99),
+                "small": {"count": int(small.sum()), "p50_ms": pct(lat[small], 50), "p99_ms": pct(lat[small], 99)},
+                "large": {"count": int((~small).sum()), "p50_ms": pct(lat[~small], 50),
+                          "p99_ms": pct(lat[~small], 99)},
+                "mean_batch": float(np.mean(batch)), "wall_s": wall, "hbm_budget_bytes": int(st["hbm_budget_bytes"])}
 
     main = replay(rate_hz, n_requests, 0)
     out = {"workload": "serving-periodic-p10 (Poisson arrivals, N log-uniform in [1000, 200000], +-1)",
-           "lanes": lanes, "max_batch": max_batch, "offered": main}
+           "lanes": lanes, "express_lanes": express_lanes, "express_max_n": express_max_n, "max_batch": max_batch,
+           "alone_ms": dict(zip(map(str, sizes_ref), alone)), "offered": main}
     if sweep:
         cap = main["systems_per_s"]
         out["sweep"] = [replay(f * cap, max(20, int(n_requests * 0.3)), k + 1)

@@ -174,6 +174,15 @@ int hsma_plan_set_precision(hsma_plan_t plan, int precision);
  * memory for n x (shifts of Rs + skin) candidate entries. */
 int hsma_plan_set_inset_skin(hsma_plan_t plan, double skin);
 
+/* Launch the near-field pair work of later steps as one CTA per work item
+ * (on = 1) instead of a persistent grid that pulls items until none are
+ * left (on = 0, the default, faster alone).  CTAs that finish their item
+ * free their SM, so work on a stream of higher priority (another plan, a
+ * serving lane) starts between items instead of after the whole step; the
+ * tensor-core fit then also uses a quarter of the SMs.  Results are the
+ * same up to the fit's grouping of sums.  No counterpart in the paper. */
+int hsma_plan_set_preemptible(hsma_plan_t plan, int on);
+
 /* Counts of the plan's single-system steps since creation: in-set lists
  * built, steps that reused a list, and steps redone because the list was
  * stale.  Any pointer may be NULL. */
@@ -331,8 +340,12 @@ int hsma_plan_load_tuning(hsma_plan_t plan, const char *cache_path);
  * hsma_plan_footprint -- and runs them as one batched update step.  Requests
  * that arrive while other lanes are busy are admitted by the next free lane,
  * so their device work overlaps.  A request larger than the whole budget
- * fails with HSMA_E_CAPACITY.  Thread-safe: submit and result may be called
- * from any host thread. */
+ * fails with HSMA_E_CAPACITY.  Small requests (see express_lanes) queue
+ * apart and have lanes of their own on a high-priority stream, while the
+ * bulk lanes' pair work is preemptible (hsma_plan_set_preemptible), so a
+ * small request waits for work items of a large batch, not for the whole
+ * batch.  Thread-safe: submit and result may be called from any host
+ * thread. */
 typedef struct hsma_server_s *hsma_server_t;
 
 typedef struct {
@@ -340,6 +353,13 @@ typedef struct {
     int max_batch;            /* systems per batched pass, 1..65528 (default 64)          */
     int lanes;                /* concurrent batched passes, 1..16 (default 2)            */
     int precision;            /* hsma_precision of served requests (default 1)           */
+    int express_lanes;        /* lanes that serve only small requests, on the stream of
+                                 highest priority, 0..lanes-1 (default 1); the others
+                                 (bulk) serve the large ones (all, if 0), on the
+                                 stream of lowest priority, with preemptible pair
+                                 work; an express lane's workspace is allocated at
+                                 creation for max_batch requests of express_max_n   */
+    int64_t express_max_n;    /* requests with n <= this are small (default 20000)     */
 } hsma_server_opts;
 
 typedef struct {

@@ -105,6 +105,7 @@ struct hsma_plan_s {
     double Rs, R0, dr, alpha, cond;
     double far_rel = 1.0 / 15.0;  // near/far threshold of the FP32 pair sums, in units of Rs
     int stall_test = 0;           // HSMA_TEST_STALL_WAIT=1 at plan creation: exercise the timeout path
+    int preemptible = 0;          // pair work as one CTA per item (see hsma_plan_set_preemptible)
     int far_field = 0;            // 0: surface images (Sec. II.B); 1: direct series at the particles
     int precision, use_graphs, profile, mon_faces;
     cudaStream_t stream;
@@ -242,6 +243,11 @@ int ensure_pinned(hsma_plan_s *p, size_t bytes)
     p->hpin_cap = nb;
     return HSMA_OK;
 }
+
+// CTAs of the cooperative tensor-core fit: one per SM, or a quarter of the
+// SMs for a preemptible plan (a cooperative launch needs all its CTAs
+// resident at once, which a smaller grid finds sooner beside other work).
+int fit_ctas(const hsma_plan_s *p) { return p->preemptible ? std::max(8, p->num_sms / 4) : p->num_sms; }
 
 // Work decomposition of a batch: targets per block, source chunks per system,
 // work items, surface blocks.  Pure host arithmetic.
@@ -404,7 +410,7 @@ size_t carve_workspace(const hsma_plan_s *p, const BatchShape &sh, int precision
     w->status = c.take<int>(sh.nsys);
     w->ctrl = c.take<int>(8);
     w->sys = c.take<SysDesc>(sh.nsys);
-    w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys, p->num_sms))
+    w->tc_work = (precision == HSMA_FP32_TC_FIT) ? (float *)c.take<char>(tc_work_bytes(p->K, p->ncols, sh.nsys, fit_ctas(p)))
                                                   : nullptr;
     w->idx64 = c.take<long long>(sh.n_total);
     w->cen = c.take<double4_32a>(sh.n_total);
@@ -595,7 +601,8 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     pa.next_item = w.ctrl;
     pa.status = w.status;
     const int ctas = tuned_ctas(p, prec, sh.variant);
-    const int grid = std::max(1, std::min(sh.items, p->num_sms * ctas));
+    pa.one_item = p->preemptible ? 1 : 0;
+    const int grid = p->preemptible ? std::max(1, sh.items) : std::max(1, std::min(sh.items, p->num_sms * ctas));
     if ((rc = launch_pair(pa, prec, sh.variant, grid, st))) return rc;
     record(p, st, 2);
     if ((rc = launch_partial_reduce(w.sys, nsys, sh.max_tgt, p->nmon, w.partials, prec, w.phi_tgt, w.e_part, st)))
@@ -605,7 +612,7 @@ int enqueue_update(hsma_plan_s *p, const BatchShape &sh, const Workspace &w, int
     // (c) fit
     if (prec == HSMA_FP32_TC_FIT)
         rc = launch_fit_tc(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->tc_mdf, w.phi_tgt,
-                           p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
+                           p->mon_inv, w.b, w.A, w.tc_work, w.status, fit_ctas(p), st);
     else
         rc = launch_fit_fp64(w.sys, nsys, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A,
                              st);
@@ -1055,7 +1062,7 @@ int run_shard(hsma_plan_s *p, const hsma_particles *x, bool far_stage, int part,
                                       st));
         if (prec == HSMA_FP32_TC_FIT)
             rc = launch_fit_tc(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->tc_hi, p->tc_lo, p->tc_mdf, w.phi_tgt,
-                               p->mon_inv, w.b, w.A, w.tc_work, w.status, p->num_sms, st);
+                               p->mon_inv, w.b, w.A, w.tc_work, w.status, fit_ctas(p), st);
         else
             rc = launch_fit_fp64(w.sys, 1, p->bc, p->K, p->ncols, p->Nb, p->Mp, w.phi_tgt, p->mon_inv, w.b, w.A, st);
         if (rc) return rc;
@@ -1160,6 +1167,22 @@ int plan_params(const double box[3], int bc, int p, double R, int Q, int Kmon, c
 }
 
 }  // namespace
+
+int hsma::plan_reserve(hsma_plan_t p, int nsys, long long n_each)
+{
+    if (!p || nsys < 1 || nsys > kMaxSystems || n_each < 1 || n_each > kMaxInsetSlots / p->nshifts)
+        return HSMA_E_ARG;
+    std::vector<long long> n(nsys, n_each);
+    BatchShape sh;
+    shape_batch(p, nsys, n.data(), p->precision, choose_tuning(p, nsys, n.data()), &sh);
+    if (sh.items < 0 || sh.surf_items < 0) return HSMA_E_ARG;
+    Workspace w;
+    int rc = ensure_workspace(p, carve_workspace(p, sh, p->precision, true, true, nullptr, &w));
+    if (rc) return rc;
+    const size_t pin_bytes = align_up(sizeof(SysDesc) * nsys, 64) + align_up(sizeof(double) * nsys, 64) +
+                             align_up(sizeof(long long) * nsys, 64) + align_up(sizeof(int) * nsys, 64);
+    return ensure_pinned(p, pin_bytes);
+}
 
 void hsma::plan_trim_workspace(hsma_plan_t p, size_t max_keep)
 {
@@ -1513,6 +1536,17 @@ int hsma_plan_set_inset_skin(hsma_plan_t pl, double skin)
     }
     pl->md_skin = skin;
     pl->md_valid = false;
+    return HSMA_OK;
+}
+
+int hsma_plan_set_preemptible(hsma_plan_t pl, int on)
+{
+    if (!pl || (on != 0 && on != 1)) return HSMA_E_ARG;
+    if (pl->preemptible != on) {
+        cudaStreamSynchronize(pl->stream ? pl->stream : pl->priv_stream);
+        drop_graphs(pl);  // the captured launches change shape
+        pl->preemptible = on;
+    }
     return HSMA_OK;
 }
 

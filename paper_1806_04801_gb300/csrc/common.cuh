@@ -390,6 +390,8 @@ struct PairArgs {
     const float4 *ext_boxes = nullptr;  // box of every block of external targets, or null
     int stall_test = 0;             // test hook: wait on a barrier nothing arrives at (bounded)
     float far2 = 0.f;               // tiles at least sqrt(far2) from the target block skip the low words
+    int one_item = 0;               // 1: CTA b does work item b and exits (grid = total_items), so that
+                                    // work on other streams gets SMs between items
     float4 *partials;       // 2 x float4 (FP32) or 1 x double4_32a (FP64) per record
     int *next_item;
     int *status;
@@ -427,6 +429,10 @@ int launch_finalize(const SysDesc *sys, int nsys, long long max_n, const int *pe
 // api.cu: free a plan's workspace when it holds more than max_keep bytes
 // (used by the serving lanes to stay inside their memory budget).
 void plan_trim_workspace(hsma_plan_t plan, size_t max_keep);
+// api.cu: allocate a plan's workspace and pinned staging for a batch of nsys
+// systems of n_each particles now (so that calls up to that size allocate
+// nothing; allocation and freeing synchronise the device)
+int plan_reserve(hsma_plan_t plan, int nsys, long long n_each);
 
 // tc_fit.cu: the tensor-core fit.  Mp_hi / Mp_lo: M+ as two BF16 words;
 // Mdf: M (K x n_cols) as FP32 word pairs (prepare_tc_operands fills all of

@@ -4,7 +4,9 @@
 // most time-consuming calculations").
 //
 // Work decomposition: one persistent grid pulls items (system, target block,
-// source chunk) from an atomic counter.  A CTA stages the chunk's sources in
+// source chunk) from an atomic counter (or, in the one-item mode of serving
+// lanes, CTA b does item b and exits, so that higher-priority work on other
+// streams gets SMs between items).  A CTA stages the chunk's sources in
 // shared-memory tiles with 1-D bulk copies (cp.async.bulk, completion on an
 // mbarrier, two buffers in flight) and every thread sums the tile into the
 // registers of its T targets.  Each item writes one partial record per target;
@@ -276,8 +278,8 @@ __global__ void __launch_bounds__(kThreads, MINB) pair_fp32_kernel(PairArgs a)
         return;
     }
 
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.next_item, 1);
+    for (int round = 0;; ++round) {
+        if (tid == 0) s_item = a.one_item ? (round == 0 ? (int)blockIdx.x : a.total_items) : atomicAdd(a.next_item, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= a.total_items || s_abort) break;
@@ -547,8 +549,8 @@ __global__ void __launch_bounds__(kThreads, 4) pair_fp64_kernel(PairArgs a)
     __syncthreads();
     uint32_t parity[2] = {0u, 0u};
 
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.next_item, 1);
+    for (int round = 0;; ++round) {
+        if (tid == 0) s_item = a.one_item ? (round == 0 ? (int)blockIdx.x : a.total_items) : atomicAdd(a.next_item, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= a.total_items || s_abort) break;

@@ -5,11 +5,19 @@
 // pseudo-inverse stay resident) with its own stream and workspace.  A free
 // lane takes the oldest waiting requests that fit -- at most max_batch systems
 // and, together with the work the other lanes hold, at most the HBM budget --
-// and runs them as one batched update step (one persistent launch over all of
-// their work items).  Requests that arrive while other lanes are on the GPU
-// are admitted by the next free lane, so their device work overlaps with the
-// batches in flight.  A request that alone exceeds the budget fails with
-// HSMA_E_CAPACITY.  Each system's arithmetic depends only on its own inputs
+// and runs them as one batched update step.  Requests that arrive while other
+// lanes are on the GPU are admitted by the next free lane, so their device
+// work overlaps with the batches in flight.  A request that alone exceeds the
+// budget fails with HSMA_E_CAPACITY.
+//
+// Small requests (n <= express_max_n) queue apart from large ones.  The
+// first express_lanes lanes serve only small requests, on the stream of
+// highest priority, with persistent launches; the other (bulk) lanes serve
+// only large requests (all requests when there is no express lane), on the
+// stream of lowest priority, with their pair work launched as one CTA per
+// work item (hsma_plan_set_preemptible): as bulk CTAs finish their items the
+// SMs go to the express lanes' pending work, so a small request waits for
+// work items of a large batch, not for the whole batch.  Each system's arithmetic depends only on its own inputs
 // and on how its sources are split into chunks, so a result is the same,
 // within rounding of the chunk grouping, alone or in a mix.
 #include <string.h>
@@ -51,7 +59,7 @@ struct hsma_server_s {
     std::vector<size_t> held;  // device bytes each lane holds for its current batch
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue;
+    std::deque<Request *> queue, queue_small;  // large / small requests, oldest first
     std::unordered_map<int64_t, Request *> all;
     int64_t next_id = 1;
     bool stop = false;
@@ -67,25 +75,37 @@ void lane_main(hsma_server_s *s, int lane)
 {
     cudaSetDevice(s->device);
     hsma_plan_t plan = s->plans[lane];
+    const bool express = lane < s->opts.express_lanes;
     std::vector<int64_t> offsets;
     std::vector<double> xyz, q, energies, forces;
     std::vector<int> status;
+    // the queue this lane takes from: express lanes the small requests, bulk
+    // lanes the large ones (and the small ones too when there is no express
+    // lane); a small request on a bulk lane would run at the low priority
+    // beside large work
+    const bool bulk_takes_small = s->opts.express_lanes == 0;
+    auto pick = [&]() -> std::deque<Request *> * {
+        if (express) return s->queue_small.empty() ? nullptr : &s->queue_small;
+        if (!s->queue.empty()) return &s->queue;
+        return (bulk_takes_small && !s->queue_small.empty()) ? &s->queue_small : nullptr;
+    };
     for (;;) {
         std::vector<Request *> batch;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
-            if (s->stop && s->queue.empty()) return;
+            s->cv_work.wait(lk, [&] { return s->stop || pick() != nullptr; });
+            std::deque<Request *> *qu = pick();
+            if (!qu) return;  // stopping, and nothing left that this lane serves
             size_t others = 0;
             for (size_t l = 0; l < s->held.size(); ++l)
                 if ((int)l != lane) others += s->held[l];
             size_t used = 0;
-            while (!s->queue.empty() && (int)batch.size() < s->opts.max_batch) {
-                Request *r = s->queue.front();
+            while (!qu->empty() && (int)batch.size() < s->opts.max_batch) {
+                Request *r = qu->front();
                 size_t one = 0;
                 hsma_plan_footprint(plan, r->n, &one);
                 if (one > s->opts.hbm_budget_bytes) {  // can never run
-                    s->queue.pop_front();
+                    qu->pop_front();
                     r->status = HSMA_E_CAPACITY;
                     r->t_done = Clock::now();
                     r->t_start = r->t_done;
@@ -94,7 +114,7 @@ void lane_main(hsma_server_s *s, int lane)
                     continue;
                 }
                 if (others + used + one > s->opts.hbm_budget_bytes) break;  // wait for memory
-                s->queue.pop_front();
+                qu->pop_front();
                 used += one;
                 batch.push_back(r);
             }
@@ -129,11 +149,15 @@ void lane_main(hsma_server_s *s, int lane)
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->held[lane] = 0;
-            // keep this lane's cached workspace within what the budget leaves
-            size_t others_now = 0;
-            for (size_t l = 0; l < s->held.size(); ++l) others_now += s->held[l];
-            size_t room = s->opts.hbm_budget_bytes > others_now ? s->opts.hbm_budget_bytes - others_now : 0;
-            hsma::plan_trim_workspace(plan, room / s->plans.size());
+            // keep a bulk lane's cached workspace within what the budget leaves
+            // (express lanes keep the workspace reserved at creation: freeing
+            // and growing it would synchronise the device behind bulk work)
+            if (!express) {
+                size_t others_now = 0;
+                for (size_t l = 0; l < s->held.size(); ++l) others_now += s->held[l];
+                size_t room = s->opts.hbm_budget_bytes > others_now ? s->opts.hbm_budget_bytes - others_now : 0;
+                hsma::plan_trim_workspace(plan, room / s->plans.size());
+            }
             s->batches++;
             s->batched_systems += nb;
             for (int i = 0; i < nb; ++i) {
@@ -173,6 +197,8 @@ int hsma_server_opts_default(hsma_server_opts *o)
     o->max_batch = 64;
     o->lanes = 2;
     o->precision = HSMA_FP32_ACC64;
+    o->express_lanes = 1;
+    o->express_max_n = 20000;
     return HSMA_OK;
 }
 
@@ -185,6 +211,8 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
     hsma_server_opts_default(&o);
     if (opts) o = *opts;
     if (o.lanes < 1 || o.lanes > 16 || o.max_batch < 1 || o.max_batch > 65528) return HSMA_E_ARG;
+    if (o.express_lanes < 0 || (o.express_lanes > 0 && o.express_lanes >= o.lanes) || o.express_max_n < 0)
+        return HSMA_E_ARG;  // at least one bulk lane serves the large requests
     if (o.hbm_budget_bytes == 0) {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return HSMA_E_CUDA;
@@ -199,9 +227,16 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
     hsma_opts po;
     hsma_opts_default(&po);
     po.precision = o.precision;
+    po.use_graphs = 0;  // batch shapes change from call to call: direct launches
+    int prio_low = 0, prio_high = 0;  // numerically: greatest priority is the lowest number
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        delete s;
+        return HSMA_E_CUDA;
+    }
     for (int l = 0; l < o.lanes; ++l) {
+        const bool express = l < o.express_lanes;
         cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, express ? prio_high : prio_low) != cudaSuccess) {
             hsma_server_destroy(s);
             return HSMA_E_CUDA;
         }
@@ -209,7 +244,13 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
         po.stream = st;
         hsma_plan_t pl = nullptr;
         int rc = hsma_plan(&pl, box, bc, p, R, Q, Kmon, &po);
+        if (!rc && !express) rc = hsma_plan_set_preemptible(pl, 1);
+        // an express lane never allocates while serving: its workspace holds
+        // a full batch of the largest small requests from the start
+        if (!rc && express && o.express_max_n > 0)
+            rc = hsma::plan_reserve(pl, o.max_batch, o.express_max_n);
         if (rc) {
+            if (pl) hsma_plan_destroy(pl);
             hsma_server_destroy(s);
             return rc;
         }
@@ -241,10 +282,10 @@ int hsma_server_submit(hsma_server_t s, int64_t n, const double *xyz, const doub
             s->t0_set = true;
         }
         s->all[r->id] = r;
-        s->queue.push_back(r);
+        (n <= s->opts.express_max_n ? s->queue_small : s->queue).push_back(r);
         *ticket = r->id;
     }
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();
     return HSMA_OK;
 }
 
@@ -282,16 +323,17 @@ int hsma_server_cancel(hsma_server_t s, int64_t ticket)
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return HSMA_E_NOT_FOUND;
     Request *r = it->second;
-    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-        if (*q == r) {
-            s->queue.erase(q);
-            r->status = HSMA_E_CANCELLED;
-            r->t_done = Clock::now();
-            r->t_start = r->t_done;
-            s->cancelled++;
-            s->cv_done.notify_all();
-            return HSMA_OK;
-        }
+    for (auto *qu : {&s->queue, &s->queue_small})
+        for (auto q = qu->begin(); q != qu->end(); ++q)
+            if (*q == r) {
+                qu->erase(q);
+                r->status = HSMA_E_CANCELLED;
+                r->t_done = Clock::now();
+                r->t_start = r->t_done;
+                s->cancelled++;
+                s->cv_done.notify_all();
+                return HSMA_OK;
+            }
     return HSMA_E_AGAIN;  // already running or finished
 }
 
@@ -302,7 +344,7 @@ int hsma_server_stats(hsma_server_t s, hsma_server_stats_t *st)
     st->completed = s->completed;
     st->failed = s->failed;
     st->cancelled = s->cancelled;
-    st->queued = (int64_t)s->queue.size();
+    st->queued = (int64_t)(s->queue.size() + s->queue_small.size());
     st->batches = s->batches;
     st->mean_batch = s->batches ? (double)s->batched_systems / s->batches : 0.0;
     st->elapsed_s = s->t0_set ? std::chrono::duration<double>(s->t_last_done - s->t0).count() : 0.0;

@@ -89,6 +89,7 @@ SIGNATURES = {
     "hsma_kernel_launches": (_I64, []),
     "hsma_allocation_calls": (_I64, []),
     "hsma_plan_set_inset_skin": (_I, [_VP, _D]),
+    "hsma_plan_set_preemptible": (_I, [_VP, _I]),
     "hsma_plan_inset_stats": (_I, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "hsma_fp32_peak": (_I, [_VP, _VP]),
     "hsma_last_timings": (_I, [_VP, _VP, _I]),
@@ -379,6 +380,10 @@ class Plan:
         the last build (0 switches reuse off)."""
         _check(_lib().hsma_plan_set_inset_skin(self._h, float(skin)), "hsma_plan_set_inset_skin")
 
+    def set_preemptible(self, on: bool):
+        """hsma_plan_set_preemptible: pair work as one CTA per work item."""
+        _check(_lib().hsma_plan_set_preemptible(self._h, 1 if on else 0), "hsma_plan_set_preemptible")
+
     def inset_stats(self) -> dict:
         """hsma_plan_inset_stats: in-set lists built, steps that reused one,
         steps redone because the list was stale."""
@@ -543,7 +548,7 @@ def basis(pts, p: int, Rs: float, stream=None):
 class hsma_server_opts(ctypes.Structure):
     """Mirror of hsma_server_opts (include/hsma.h)."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("lanes", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("express_lanes", ctypes.c_int), ("express_max_n", ctypes.c_int64)]
 
 
 class hsma_request_info(ctypes.Structure):
@@ -576,7 +581,8 @@ class Server:
     """hsma_server_*: continuous-batching request loop over resident plans."""
 
     def __init__(self, box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64, lanes: int = 2,
-                 max_batch: int = 64, hbm_budget_bytes: int = 0):
+                 max_batch: int = 64, hbm_budget_bytes: int = 0, express_lanes: int | None = None,
+                 express_max_n: int | None = None):
         L = _lib()
         o = hsma_server_opts()
         _check(L.hsma_server_opts_default(ctypes.byref(o)), "hsma_server_opts_default")
@@ -584,6 +590,12 @@ class Server:
         o.lanes = int(lanes)
         o.max_batch = int(max_batch)
         o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if express_lanes is not None:
+            o.express_lanes = int(express_lanes)
+        else:  # the default, as far as lanes allow (one lane at least is bulk)
+            o.express_lanes = min(int(o.express_lanes), int(lanes) - 1)
+        if express_max_n is not None:
+            o.express_max_n = int(express_max_n)
         box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
         h = ctypes.c_void_p()
         _check(L.hsma_server_create(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon),

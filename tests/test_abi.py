@@ -128,6 +128,7 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
     assert lib.hsma_plan_set_precision(None, 0) == ARG
     assert lib.hsma_plan_set_inset_skin(None, ctypes.c_double(0.05)) == ARG
     assert lib.hsma_plan_inset_stats(None, None, None, None) == ARG
+    assert lib.hsma_plan_set_preemptible(None, 1) == ARG
     buf = (ctypes.c_double * 8)()
     assert lib.hsma_plan_get_matrix(None, 0, buf, 8) == ARG
     assert lib.hsma_last_timings(None, buf, 8) == ARG

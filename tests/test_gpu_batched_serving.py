@@ -219,3 +219,51 @@ def test_serving_cancellation():
         st = srv.stats()
         assert st["cancelled"] == sum(1 for c in codes.values() if c == 0) >= 1
         assert st["completed"] + st["cancelled"] == len(reqs)
+
+
+def test_preemptible_pair_work_gives_the_same_results():
+    """One CTA per work item (the serving bulk lanes' mode) against the
+    persistent grid: the same items and the same fixed-order reduction, so
+    the FP32 pair sums with the FP64 fit are bit-identical."""
+    w = I.BATCH_PERIODIC
+    systems = [I.uniform_pm1(int(n), w.box, seed_offset=140 + i) for i, n in enumerate([900, 5000, 20000])]
+    xyz = np.concatenate([s[0] for s in systems])
+    q = np.concatenate([s[1] for s in systems])
+    off = np.concatenate([[0], np.cumsum([len(s[1]) for s in systems])])
+    dx, dq = to_dev(xyz, q)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        E0, F0, _, _ = plan.energy_forces_batched(dx, dq, off)
+        plan.set_preemptible(True)
+        E1, F1, _, _ = plan.energy_forces_batched(dx, dq, off)
+        assert np.array_equal(E0, E1) and bool((F0 == F1).all())
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32_tc") as plan:
+        E0, F0, _, _ = plan.energy_forces_batched(dx, dq, off)
+        plan.set_preemptible(True)  # the tensor-core fit on a quarter of the SMs: other sum grouping
+        E1, F1, _, _ = plan.energy_forces_batched(dx, dq, off)
+        for i in range(len(systems)):
+            assert rel_energy_err(E1[i], E0[i], systems[i][1]) <= 1e-7
+
+
+def test_small_request_overtakes_a_large_batch():
+    """Express lane (high-priority stream) and bulk lane (preemptible pair
+    work): a small request submitted while a large one runs finishes long
+    before it, and both agree with direct calls."""
+    import time
+    w = I.SERVING_PERIODIC
+    big = I.uniform_pm1(200000, w.box, seed_offset=150)
+    small = I.uniform_pm1(2000, w.box, seed_offset=151)
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=2, max_batch=4,
+                     express_lanes=1, express_max_n=20000) as srv:
+        tb = srv.submit(*big)
+        time.sleep(0.03)  # the large request is on the GPU
+        ts = srv.submit(*small)
+        code_s, E_s, F_s, info_s = srv.result(ts)
+        code_b, E_b, F_b, info_b = srv.result(tb)
+    assert code_s == 0 and code_b == 0
+    print(f"\nlarge request {info_b['latency_ms']:.1f} ms, small request behind it {info_s['latency_ms']:.1f} ms")
+    assert info_s["latency_ms"] < 0.5 * (info_b["latency_ms"] - 30.0), (info_s, info_b)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        for (sx, sq), E, F in ((small, E_s, F_s), (big, E_b, F_b)):
+            U1, F1, _, _ = plan.energy_forces(sx, sq)
+            assert rel_energy_err(E, U1, sq) <= TOL["fp32"]["energy"]
+            assert rms(F - F1) <= TOL["fp32"]["force_rms"] * rms(F1)

@@ -447,10 +447,17 @@ int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const dou
                             double *field, int precision, void *stream);
 
 /* Harmonic basis of Eq. "harmonic" at np points (device pointers; pts
- * np x 3, out np x (p+1)^2 row-major): the orthonormal real solid harmonics
- * (|x|/Rs)^n Y_nm, index k = n^2 + n + m, m > 0 the cosine and m < 0 the sine
- * part, without the Condon-Shortley phase.  Errors: HSMA_E_ARG, HSMA_E_CUDA. */
-int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, void *stream);
+ * np x 3, out np x (p+1)^2 row-major, FP64): the orthonormal real solid
+ * harmonics (|x|/Rs)^n Y_nm, index k = n^2 + n + m, m > 0 the cosine and
+ * m < 0 the sine part, without the Condon-Shortley phase; 0 <= p <= 40.
+ * precision HSMA_FP64: the recurrence in FP64 (relative error ~1e-16 of the
+ * row's scale (|x|/Rs)^n); HSMA_FP32_ACC64: the same recurrence, fully
+ * normalised, in double-float arithmetic (pairs of FP32 words) on the FP32
+ * pipe, several times faster on this part and accurate to ~1e-14 of that
+ * scale.  Each point is scaled by a power of two first, so neither form
+ * underflows for points near the origin.  Returns once out holds the basis.
+ * Errors: HSMA_E_ARG (p, Rs, np, null pointers, precision), HSMA_E_CUDA. */
+int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, int precision, void *stream);
 
 /* ------------------------------------------------------ device peaks */
 /* Measured FP32 throughput of the current device (no counterpart in the

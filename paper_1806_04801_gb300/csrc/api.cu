@@ -1951,10 +1951,17 @@ int hsma_coulomb_sum(int64_t ns, const double *src, int64_t nt, const double *tg
     return rc;
 }
 
-int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, void *stream)
+int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, int precision, void *stream)
 {
     if (p < 0 || p > 40 || !(Rs > 0) || np < 1 || !pts || !out) return HSMA_E_ARG;
+    if (precision != HSMA_FP64 && precision != HSMA_FP32_ACC64) return HSMA_E_ARG;
     int Nb = (p + 1) * (p + 1);
+    if (precision == HSMA_FP32_ACC64) {
+        cudaStream_t st = (cudaStream_t)stream;
+        int rc = launch_basis_df(p, Rs, np, pts, 3, out, Nb, st);
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
+        return rc;
+    }
     auto nt = norm_table(p);
     double *dn = nullptr;
     cudaStream_t st = (cudaStream_t)stream;

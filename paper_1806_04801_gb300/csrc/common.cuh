@@ -296,6 +296,9 @@ int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *out64
 int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st);
 int launch_basis(int P, double Rs, long long np, const double *pts, int pts_stride, const double *norm,
                  double *out, long long ld, cudaStream_t st);
+// the same basis in double-float arithmetic on the FP32 pipe (no norm table)
+int launch_basis_df(int P, double Rs, long long np, const double *pts, int pts_stride, double *out, long long ld,
+                    cudaStream_t st);
 int launch_fitting_matrix(int K, int Nb, int ncols, int drop, const double *Bx, const double *Bxt,
                           double *Mcol, double *Mrow, cudaStream_t st);
 int build_pseudo_inverse(int K, int n, double *Wcol, double *Mp, double *cond, int *rank_ok,

@@ -3,6 +3,8 @@
 // pseudo-inverse of the fitting matrix by Householder QR.
 #include <math.h>
 
+#include <cmath>
+
 #include <vector>
 
 #include "common.cuh"
@@ -179,6 +181,306 @@ __global__ void __launch_bounds__(kBasisThreads) basis_kernel(int P, double inv_
             }
             two_m_1 += 2.0;
         }
+    }
+}
+
+// ------------------------------------------- double-float basis evaluation
+// Double-float numbers v = hi + lo (two FP32 words, |lo| <= ulp(hi)/2), for
+// the basis on the FP32 pipe: GB300 issues FP64 at a small fraction of its
+// FP32 rate.  Products follow Dekker's method, the exact error of hi*hi taken
+// with one fused multiply-add (TwoProd), the cross terms added to it; both
+// products and sums end with Fast2Sum, so every result is a normalised pair.
+// Relative error about 2^-46 per operation.
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float s = __fadd_rn(p, e);
+    return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
+}
+
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b)
+{
+    return df_add_df(a, make_float2(-b.x, -b.y));
+}
+
+// a u - b v in one pass: the two leading products and their exact errors
+// (TwoProd), TwoSum of the leading products, the errors and the four cross
+// terms gathered in FP32, one Fast2Sum.  Same accuracy as two products and a
+// difference, in fewer operations.
+__device__ __forceinline__ float2 df_dot2_sub(float2 a, float2 u, float2 b, float2 v)
+{
+    const float p = __fmul_rn(a.x, u.x), q = __fmul_rn(b.x, v.x);
+    const float ep = __fmaf_rn(a.x, u.x, -p), eq = __fmaf_rn(b.x, v.x, -q);
+    const float s = __fsub_rn(p, q);
+    const float bb = __fsub_rn(s, p);
+    float e = __fsub_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fadd_rn(q, bb));
+    e = __fadd_rn(e, __fsub_rn(ep, eq));
+    e = __fmaf_rn(a.x, u.y, e);
+    e = __fmaf_rn(a.y, u.x, e);
+    e = __fmaf_rn(-b.x, v.y, e);
+    e = __fmaf_rn(-b.y, v.x, e);
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+
+__device__ __forceinline__ float2 df_of(double v)
+{
+    float h, l;
+    split_f64(v, h, l);
+    return make_float2(h, l);
+}
+
+// FP64 value of (hi + lo) * 2^k for a normalised pair, assembled in integer
+// arithmetic (an FP64 addition of the two words would run on the slow FP64
+// pipe).  hi's sign, exponent + k and significand give the FP64 bit pattern
+// (kb = (896 + k) << 20 rebiases the exponent field); lo, scaled by an FP32
+// power of two to FP64 units of hi's binade and rounded to an integer, is
+// added to the pattern's magnitude (negative: subtracted).  A carry out of
+// the significand raises the exponent, which is exactly the IEEE layout's
+// behaviour; where hi is a power of two and lo points below it the sum lies
+// in the binade underneath, whose spacing is half as large, so lo is counted
+// in those units.  A hi below 2^-74 (that is, below 2^-74 of the point's
+// scale: the kernel scales every point to a largest coordinate in [1, 2))
+// gives a signed zero.  kChecked adds the range checks for exponent offsets
+// that can leave FP64's normal range (result zero below it, infinity above);
+// points of ordinary size never need them.
+template <bool kChecked>
+__device__ __forceinline__ double df_to_f64_scaled(float2 v, uint32_t kb, int k)
+{
+    const uint32_t bh = __float_as_uint(v.x), bl = __float_as_uint(v.y);
+    const uint32_t sign = bh & 0x80000000u, mag = bh ^ sign;
+    const uint32_t eh = mag >> 23;
+    const uint32_t down = (uint32_t)((mag & 0x7fffffu) == 0u) & ((bh ^ bl) >> 31);
+    // 1 / (FP64 unit of hi's binade) = 2^(179 - eh): FP32 exponent field
+    // 306 - eh (<= 254 for eh >= 53), with hi's sign
+    const float pw = __uint_as_float(((306u - eh + down) << 23) | sign);
+    const int d = __float2int_rn(__fmul_rn(v.y, pw));  // |d| <= 2^28 for a normalised pair
+    unsigned long long bits =
+        (((unsigned long long)(((mag >> 3) + kb) | sign) << 32) | (unsigned long long)(bh << 29)) +
+        (unsigned long long)(long long)d;
+    if (eh < 53u) bits = (unsigned long long)sign << 32;
+    if (kChecked) {
+        const int ed = (int)eh + 896 + k;
+        if (ed <= 0) bits = (unsigned long long)sign << 32;
+        if (ed >= 2047) bits = (unsigned long long)(sign | 0x7ff00000u) << 32;
+    }
+    return __longlong_as_double((long long)bits);
+}
+
+// The same orthonormal real solid harmonics as basis_kernel, in double-float
+// arithmetic on the FP32 pipe, by the fully normalised form of the recurrence:
+// with Pbar_n^m = norm(n, m) Pi_n^m,
+//   Pbar_m^m     = D_m,   D_0 = 1/sqrt(4 pi),
+//                         D_m = D_{m-1} sqrt((2m+1)/(2m)) (times sqrt 2 at m = 1),
+//   Pbar_{m+1}^m = sqrt(2m+3) D_m z,
+//   Pbar_n^m     = a_nm z Pbar_{n-1}^m - b_nm r2 Pbar_{n-2}^m,
+//     a_nm = sqrt((4n^2 - 1) / (n^2 - m^2)),
+//     b_nm = sqrt((2n+1) ((n-1)^2 - m^2) / ((2n-3) (n^2 - m^2))),
+// (the ratios norm(n, m) (2n-1) / ((n-m) norm(n-1, m)) and
+// norm(n, m) (n+m-1) / ((n-m) norm(n-2, m)) of the unnormalised recurrence),
+// so every intermediate stays of order r^n and the norm products disappear.
+// Each point is scaled by a power of two 2^-e that brings its largest
+// coordinate (over Rs) into [1, 2): a degree-n value is then the double-float
+// result times 2^(e n), applied exactly in the FP64 assembly, so small or
+// large |x| / Rs cannot leave FP32's exponent range.  The coefficient tables
+// are computed once per block in FP64 and kept in shared memory as pairs.
+// Accuracy: relative ~1e-14 of the row's scale (r/Rs)^n per value, against
+// ~1e-16 for the FP64 kernel.
+//
+// Layout of the work: a warp takes 32 consecutive points (rows) and runs the
+// degree n in the outer loop, m inner, so that each degree completes the
+// contiguous row segment [n^2, n^2 + 2n].  The recurrence state of every m
+// (Pbar at the last two degrees, in two arrays that alternate with the
+// degree's parity, and (x + i y)^m) sits in shared memory, one slot per lane.
+// A degree's 2n + 1 values per row go to a shared staging tile; the warp then
+// stores the tile's 32 segments with its lanes over consecutive elements of
+// the tile (row r = floor(f / (2n + 1)) by a multiply-shift, exact for
+// f < 2^20 / (2n + 1)).  Rows are thus written front to back in runs of up
+// to 2P + 1 doubles: the 32-byte sectors of a row complete within one or two
+// degrees (in the m-outer order every sector of every row in flight stayed
+// partly written until the row was done, and L2 evicted and re-read them),
+// and each store instruction covers two or three row segments instead of one
+// value in each of 32 rows.
+//
+// The recurrence coefficients do not depend on P: the host computes them once
+// in FP64 for every n, m <= 40, splits them into pairs and passes them as a
+// kernel parameter; each block copies the (P+1)^2 it needs to shared memory.
+constexpr int kBasisDfWarps = 2;  // warps per block
+
+struct BasisDfTables {
+    float2 a[kBasisMaxP + 1][kBasisMaxP + 1];  // a_nm at [m][n] (n >= m + 2)
+    float2 b[kBasisMaxP + 1][kBasisMaxP + 1];  // b_nm at [m][n]
+    float2 d[kBasisMaxP + 1];                  // D_m
+    float2 e[kBasisMaxP + 1];                  // sqrt(2m + 3) D_m
+};
+
+const BasisDfTables &basis_df_tables()
+{
+    static const BasisDfTables t = [] {
+        BasisDfTables v{};
+        auto pair = [](double x) {
+            const float h = (float)x;
+            return make_float2(h, (float)(x - (double)h));
+        };
+        for (int m = 0; m <= kBasisMaxP; ++m) {
+            for (int n = m + 2; n <= kBasisMaxP; ++n) {
+                const double dn = n, dm = m, q = dn * dn - dm * dm;
+                v.a[m][n] = pair(std::sqrt((4.0 * dn * dn - 1.0) / q));
+                v.b[m][n] = pair(std::sqrt((2.0 * dn + 1.0) * ((dn - 1.0) * (dn - 1.0) - dm * dm) / ((2.0 * dn - 3.0) * q)));
+            }
+            double d = 1.0 / std::sqrt(4.0 * kPi);
+            for (int j = 1; j <= m; ++j) d *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
+            if (m > 0) d *= std::sqrt(2.0);
+            v.d[m] = pair(d);
+            v.e[m] = pair(std::sqrt(2.0 * m + 3.0) * d);
+        }
+        return v;
+    }();
+    return t;
+}
+
+__host__ __device__ constexpr size_t basis_df_smem_bytes(int P, int warps)
+{
+    // tables a, b ((P+1)^2 each), D, E (P+1 each); per warp: 4 (P+1) state
+    // slots x 32 lanes and a 32 x (2P+1) staging tile (8-byte words)
+    return 8 * ((size_t)2 * (P + 1) * (P + 1) + (size_t)2 * (P + 1) +
+                (size_t)warps * 32 * ((size_t)4 * (P + 1) + (size_t)(2 * P + 1)));
+}
+
+struct BasisDfWarp {
+    float2 *pst;    // Pbar at even, then odd degrees: slot m of this lane at [32 m]
+    float2 *cs;     // (x + i y)^m, real part, slot m at [32 m]
+    float2 *ss;     // imaginary part
+    double *stage;  // [32 rows][2P + 1]
+};
+
+// One group of up to 32 points (rows i0 .. i0 + rows - 1): the degree loop.
+template <bool kChecked>
+__device__ __forceinline__ void basis_df_rows(int P, const float2 *ta, const float2 *tb, const float2 *td,
+                                              const float2 *te, const BasisDfWarp &w, int lane, float2 X,
+                                              float2 Y, float2 Z, float2 R2, int e, int rows, double *og,
+                                              int ld)
+{
+    const int W = P + 1, pitch = 2 * P + 1;
+    float2 C = make_float2(1.f, 0.f), S = make_float2(0.f, 0.f);  // (x + i y)^n, scaled
+    double *srow = w.stage + lane * pitch;
+    for (int n = 0; n <= P; ++n) {
+        const int en = e * n;
+        const uint32_t kb = (uint32_t)(896 + en) << 20;
+        float2 *cur = w.pst + (n & 1) * 32 * W, *prv = w.pst + ((n & 1) ^ 1) * 32 * W;
+        double *sc = srow + n;  // column n + m holds the cosine part, n - m the sine part
+        if (n > 0) {
+            const float2 c2 = df_sub(df_mul(C, X), df_mul(S, Y));
+            S = df_add_df(df_mul(S, X), df_mul(C, Y));
+            C = c2;
+        }
+        w.cs[32 * n] = C;
+        w.ss[32 * n] = S;
+        {  // m = n
+            const float2 pd = td[n];
+            cur[32 * n] = pd;
+            sc[n] = df_to_f64_scaled<kChecked>(df_mul(pd, C), kb, en);
+            if (n > 0) sc[-n] = df_to_f64_scaled<kChecked>(df_mul(pd, S), kb, en);
+        }
+        if (n > 0) {  // m = n - 1
+            const int m = n - 1;
+            const float2 p = df_mul(te[m], Z);
+            cur[32 * m] = p;
+            if (m == 0) {
+                sc[0] = df_to_f64_scaled<kChecked>(p, kb, en);
+            } else {
+                sc[m] = df_to_f64_scaled<kChecked>(df_mul(p, w.cs[32 * m]), kb, en);
+                sc[-m] = df_to_f64_scaled<kChecked>(df_mul(p, w.ss[32 * m]), kb, en);
+            }
+        }
+        if (n >= 2) {  // m = 0: (x + i y)^0 = 1
+            const float2 pn = df_dot2_sub(ta[n], df_mul(Z, prv[0]), tb[n], df_mul(R2, cur[0]));
+            cur[0] = pn;
+            sc[0] = df_to_f64_scaled<kChecked>(pn, kb, en);
+        }
+        // m >= 1, two orders per pass: their chains are independent, which
+        // doubles the instruction-level parallelism of the double-float work
+        int m = 1;
+        for (; m + 3 <= n; m += 2) {
+            const float2 p1a = prv[32 * m], p2a = cur[32 * m], p1b = prv[32 * m + 32], p2b = cur[32 * m + 32];
+            const float2 ca = w.cs[32 * m], sa = w.ss[32 * m], cb = w.cs[32 * m + 32], sb = w.ss[32 * m + 32];
+            const float2 pa = df_dot2_sub(ta[m * W + n], df_mul(Z, p1a), tb[m * W + n], df_mul(R2, p2a));
+            const float2 pb =
+                df_dot2_sub(ta[(m + 1) * W + n], df_mul(Z, p1b), tb[(m + 1) * W + n], df_mul(R2, p2b));
+            cur[32 * m] = pa;
+            cur[32 * m + 32] = pb;
+            sc[m] = df_to_f64_scaled<kChecked>(df_mul(pa, ca), kb, en);
+            sc[-m] = df_to_f64_scaled<kChecked>(df_mul(pa, sa), kb, en);
+            sc[m + 1] = df_to_f64_scaled<kChecked>(df_mul(pb, cb), kb, en);
+            sc[-m - 1] = df_to_f64_scaled<kChecked>(df_mul(pb, sb), kb, en);
+        }
+        if (m + 2 <= n) {
+            const float2 p1 = prv[32 * m], p2 = cur[32 * m];
+            const float2 pn = df_dot2_sub(ta[m * W + n], df_mul(Z, p1), tb[m * W + n], df_mul(R2, p2));
+            cur[32 * m] = pn;
+            sc[m] = df_to_f64_scaled<kChecked>(df_mul(pn, w.cs[32 * m]), kb, en);
+            sc[-m] = df_to_f64_scaled<kChecked>(df_mul(pn, w.ss[32 * m]), kb, en);
+        }
+        __syncwarp();
+        const int wd = 2 * n + 1, tot = rows * wd;
+        const uint32_t cw = ((1u << 20) + (uint32_t)wd - 1u) / (uint32_t)wd;  // ceil(2^20 / (2n + 1))
+        double *ob = og + n * n;
+#pragma unroll 4
+        for (int f = lane; f < tot; f += 32) {
+            const int r = (int)(((uint32_t)f * cw) >> 20), j = f - r * wd;
+            ob[r * ld + j] = w.stage[r * pitch + j];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32 * kBasisDfWarps) basis_df_kernel(const __grid_constant__ BasisDfTables tabs,
+                                                                      int P, double inv_rs, long long np,
+                                                                      const double *__restrict__ pts, int stride,
+                                                                      double *__restrict__ out, long long ld)
+{
+    extern __shared__ float2 tab[];
+    const int W = P + 1, pitch = 2 * P + 1;
+    float2 *ta = tab, *tb = tab + W * W, *td = tab + 2 * W * W, *te = td + W;
+    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
+        const int m = t / W, n = t % W;
+        ta[t] = tabs.a[m][n];
+        tb[t] = tabs.b[m][n];
+    }
+    for (int m = threadIdx.x; m <= P; m += blockDim.x) {
+        td[m] = tabs.d[m];
+        te[m] = tabs.e[m];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *wb = te + W + (size_t)warp * 32 * (4 * W + pitch);
+    const BasisDfWarp w{wb + lane, wb + 64 * W + lane, wb + 96 * W + lane, reinterpret_cast<double *>(wb + 128 * W)};
+    const long long ngroups = (np + 31) / 32;
+    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp; g < ngroups;
+         g += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const long long i0 = g * 32;
+        const int rows = (int)min(32LL, np - i0);
+        const long long i = i0 + min(lane, rows - 1);  // lanes past the end repeat the last point, unwritten
+        const double px = pts[i * stride], py = pts[i * stride + 1], pz = pts[i * stride + 2];
+        const double big = fmax(fabs(px), fmax(fabs(py), fabs(pz))) * inv_rs;
+        const int eb = min((__double2hiint(big) >> 20) & 0x7ff, 2045);  // biased exponent of the largest
+        int e = 0;
+        double f = 0.0;  // a point at the origin (or below FP64's normal range) is the origin
+        if (eb > 0) {
+            e = eb - 1023;
+            f = inv_rs * __hiloint2double((2046 - eb) << 20, 0);  // inv_rs 2^-e
+        }
+        const float2 X = df_of(px * f), Y = df_of(py * f), Z = df_of(pz * f);
+        const float2 R2 = df_add_df(df_add_df(df_mul(X, X), df_mul(Y, Y)), df_mul(Z, Z));
+        // exponent offsets e n with n <= P stay inside FP64's range for every value of FP32 size
+        const bool plain = __all_sync(0xffffffffu, abs(e) * P <= 895);
+        if (plain)
+            basis_df_rows<false>(P, ta, tb, td, te, w, lane, X, Y, Z, R2, e, rows, out + i0 * ld, (int)ld);
+        else
+            basis_df_rows<true>(P, ta, tb, td, te, w, lane, X, Y, Z, R2, e, rows, out + i0 * ld, (int)ld);
     }
 }
 
@@ -370,6 +672,29 @@ int launch_basis(int P, double Rs, long long np, const double *pts, int stride, 
     const long long blocks = std::min<long long>((np + kBasisThreads - 1) / kBasisThreads, in_flight);
     const size_t smem = sizeof(double) * ((size_t)(P + 1) + (size_t)(P + 1) * (P + 1));
     basis_kernel<<<(unsigned)blocks, kBasisThreads, smem, st>>>(P, 1.0 / Rs, np, pts, stride, norm, out, ld);
+    HSMA_LAUNCHED();
+    HSMA_CUDA_TRY(cudaGetLastError());
+    return HSMA_OK;
+}
+
+int launch_basis_df(int P, double Rs, long long np, const double *pts, int stride, double *out, long long ld,
+                    cudaStream_t st)
+{
+    if (np <= 0) return HSMA_OK;
+    // the kernel indexes a group's 32 rows with 32-bit offsets r ld + column
+    if (P < 0 || P > kBasisMaxP || ld < (long long)(P + 1) * (P + 1) || ld > (1LL << 26)) return HSMA_E_ARG;
+    int dev = 0, sms = 1, per_sm = 0;
+    HSMA_CUDA_TRY(cudaGetDevice(&dev));
+    HSMA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = basis_df_smem_bytes(P, kBasisDfWarps);
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(basis_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HSMA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, basis_df_kernel, 32 * kBasisDfWarps, smem));
+    if (per_sm < 1) return HSMA_E_ARG;
+    const long long groups = (np + 31) / 32;
+    const long long blocks =
+        std::min<long long>((groups + kBasisDfWarps - 1) / kBasisDfWarps, (long long)sms * per_sm);
+    basis_df_kernel<<<(unsigned)blocks, 32 * kBasisDfWarps, smem, st>>>(basis_df_tables(), P, 1.0 / Rs, np, pts,
+                                                                       stride, out, ld);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

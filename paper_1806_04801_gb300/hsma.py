@@ -83,7 +83,7 @@ SIGNATURES = {
     "hsma_energy_forces_batched": (_I, [_VP, _I, _VP, ctypes.POINTER(hsma_particles), _VP, _VP, _VP, _VP]),
     "hsma_coulomb_sum": (_I, [_I64, _VP, _I64, _VP, _VP, _VP, _I, _VP]),
     "hsma_coulomb_sum_static": (_I, [_I64, _VP, _I64, _VP, _VP, _VP, _I, _VP]),
-    "hsma_basis": (_I, [_I, _D, _I64, _VP, _VP, _VP]),
+    "hsma_basis": (_I, [_I, _D, _I64, _VP, _VP, _I, _VP]),
     "hsma_strerror": (ctypes.c_char_p, [_I]),
     "hsma_version": (ctypes.c_char_p, []),
     "hsma_kernel_launches": (_I64, []),
@@ -530,8 +530,10 @@ def coulomb_sum_static(src, tgt, field=True, precision=FP32_ACC64, stream=None):
     return pot, fld
 
 
-def basis(pts, p: int, Rs: float, stream=None):
-    """hsma_basis on a torch CUDA tensor of points (np, 3)."""
+def basis(pts, p: int, Rs: float, precision: str = "fp64", stream=None):
+    """hsma_basis on a torch CUDA tensor of points (np, 3).  precision "fp64"
+    (FP64 recurrence) or "fp32" (double-float recurrence on the FP32 pipe,
+    ~1e-14 relative); the result is FP64 either way."""
     import torch
     pp, dev = _ptr_and_dev(pts)
     if not dev:
@@ -539,7 +541,10 @@ def basis(pts, p: int, Rs: float, stream=None):
     if pts.dim() != 2 or pts.shape[1] != 3:
         raise ValueError("pts must have shape (np, 3)")
     out = torch.empty((pts.shape[0], (p + 1) ** 2), dtype=torch.float64, device=pts.device)
-    _check(_lib().hsma_basis(int(p), float(Rs), pts.shape[0], pp, out.data_ptr(), _stream_handle(stream)),
+    prec = {"fp64": FP64, "fp32": FP32_ACC64}.get(precision)
+    if prec is None:
+        raise ValueError("basis precision is 'fp64' or 'fp32'")
+    _check(_lib().hsma_basis(int(p), float(Rs), pts.shape[0], pp, out.data_ptr(), prec, _stream_handle(stream)),
            "hsma_basis")
     return out
 

@@ -149,10 +149,12 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
         assert fn(2, misaligned, 2, tgt, pot, None, 1, None) == ARG
     assert lib.hsma_coulomb_sum(1 << 32, src, 2, tgt, pot, None, 1, None) == ARG
     assert lib.hsma_coulomb_sum_static(1 << 32, src, 2, tgt, pot, None, 1, None) == CAP
-    assert lib.hsma_basis(-1, 1.0, 2, tgt, buf, None) == ARG
-    assert lib.hsma_basis(41, 1.0, 2, tgt, buf, None) == ARG
-    assert lib.hsma_basis(4, 0.0, 2, tgt, buf, None) == ARG
-    assert lib.hsma_basis(4, 1.0, 0, tgt, buf, None) == ARG
+    for prec in (0, 1):
+        assert lib.hsma_basis(-1, 1.0, 2, tgt, buf, prec, None) == ARG
+        assert lib.hsma_basis(41, 1.0, 2, tgt, buf, prec, None) == ARG
+        assert lib.hsma_basis(4, 0.0, 2, tgt, buf, prec, None) == ARG
+        assert lib.hsma_basis(4, 1.0, 0, tgt, buf, prec, None) == ARG
+    assert lib.hsma_basis(4, 1.0, 2, tgt, buf, 2, None) == ARG        # FP64 or double-float only
     assert lib.hsma_fp32_peak(None, None) == ARG
 
     # serving: options and handles

@@ -116,21 +116,73 @@ def test_plan_matrices_match_oracle(small_periodic):
         assert np.all(scale > 0)
 
 
-def test_basis_entry_point():
+def _basis_points():
+    """777 normal points (several warps' groups of 32 and a ragged tail) and
+    the special rows: the origin, points on the z axis, in the x = 0 and y = 0
+    planes, 1e-20 Rs and 1e-30 Rs from the origin (values below FP64's range
+    at high degree; the double-float form takes its range-checked path for
+    the warp holding them) and 66 Rs out."""
+    g = np.random.default_rng(3)
+    special = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.8], [0.0, 0.0, -1.1], [0.0, 0.4, -0.3], [0.7, 0.0, 0.2],
+                        [3e-21, -5e-21, 2e-21], [50.0, -100.0, 25.0], [1.7, 0.0, 0.0], [1e-30, 2e-30, -1e-30]])
+    return np.concatenate([g.standard_normal((777, 3)), special])
+
+
+def _basis_reference(pts, P, Rs):
+    """Oracle basis times the orthonormalisation sqrt((2 - d_m0)(2n + 1)/(4 pi) (n-|m|)!/(n+|m|)!),
+    and the row scale sqrt(2 (2n + 1)/(4 pi)) (|x|/Rs)^n that bounds each value."""
     import math
     import oracle
-    g = np.random.default_rng(3)
-    pts = g.standard_normal((777, 3))
-    P, Rs = 12, 1.7
-    (dp,) = to_dev(pts)
-    B = hs().basis(dp, P, Rs).cpu().numpy()
     Bo = oracle.basis(pts, P, Rs)
+    rho = np.linalg.norm(pts, axis=1) / Rs
+    scale = np.empty_like(Bo)
     for n in range(P + 1):
         for m in range(-n, n + 1):
             k = n * n + n + m
             am = abs(m)
-            c = math.sqrt((2 if m else 1) * (2 * n + 1) / (4 * math.pi) * math.factorial(n - am) / math.factorial(n + am))
-            np.testing.assert_allclose(B[:, k], c * Bo[:, k], rtol=1e-11, atol=1e-13 * (np.abs(c * Bo[:, k]).max() + 1))
+            Bo[:, k] *= math.sqrt((2 if m else 1) * (2 * n + 1) / (4 * math.pi)
+                                  * math.factorial(n - am) / math.factorial(n + am))
+            with np.errstate(under="ignore"):
+                scale[:, k] = math.sqrt(2 * (2 * n + 1) / (4 * math.pi)) * rho ** n
+    return Bo, scale
+
+
+# Basis error bound relative to the row scale: FP64 recurrence a few ulps per
+# degree; double-float ~2^-46 per operation over up to 3 operations per degree
+BASIS_TOL = {"fp64": 5e-14, "fp32": 5e-12}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("P", [0, 1, 12, 25, 40])
+def test_basis_entry_point(precision, P):
+    pts = _basis_points()
+    Rs = 1.7
+    (dp,) = to_dev(pts)
+    B = hs().basis(dp, P, Rs, precision=precision).cpu().numpy()
+    ref, scale = _basis_reference(pts, P, Rs)
+    assert np.all(np.isfinite(B))
+    err = np.abs(B - ref)
+    bound = BASIS_TOL[precision] * scale + 1e-300
+    assert np.all(err <= bound), (precision, P, float(np.max(err / (scale + 1e-300))))
+    # the origin: Y_00 only, every other value exactly zero
+    assert B[777, 0] == pytest.approx(1.0 / np.sqrt(4 * np.pi), rel=1e-15) and np.all(B[777, 1:] == 0.0)
+
+
+def test_basis_double_float_and_fp64_agree_at_scale():
+    """The two forms at 2e5 points spread over the Rs ball (the plan's use:
+    monitoring points and directions inside or on the sphere)."""
+    g = np.random.default_rng(31)
+    pts = g.standard_normal((200_003, 3))
+    pts *= (g.random(len(pts)) ** (1 / 3) * 1.5 / np.linalg.norm(pts, axis=1))[:, None]
+    (dp,) = to_dev(pts)
+    P, Rs = 12, 1.5
+    B64 = hs().basis(dp, P, Rs, precision="fp64")
+    Bdf = hs().basis(dp, P, Rs, precision="fp32")
+    rho = np.linalg.norm(pts, axis=1) / Rs
+    n_of_k = np.repeat(np.arange(P + 1), 2 * np.arange(P + 1) + 1)
+    scale = np.sqrt(2 * (2 * n_of_k + 1) / (4 * np.pi))[None, :] * rho[:, None] ** n_of_k[None, :]
+    err = np.abs((Bdf - B64).cpu().numpy())
+    assert np.all(err <= BASIS_TOL["fp32"] * scale + 1e-300)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -168,14 +168,17 @@ def test_basis_entry_point(precision, P):
     assert B[777, 0] == pytest.approx(1.0 / np.sqrt(4 * np.pi), rel=1e-15) and np.all(B[777, 1:] == 0.0)
 
 
-def test_basis_double_float_and_fp64_agree_at_scale():
-    """The two forms at 2e5 points spread over the Rs ball (the plan's use:
-    monitoring points and directions inside or on the sphere)."""
-    g = np.random.default_rng(31)
-    pts = g.standard_normal((200_003, 3))
+@pytest.mark.parametrize("P,n", [(12, 200_003), (40, 40_001)])
+def test_basis_double_float_and_fp64_agree_at_scale(P, n):
+    """The two forms at many points spread over the Rs ball (the plan's use:
+    monitoring points and directions inside or on the sphere); every warp
+    takes several groups of 32 points, and at P = 40 one block fills an SM's
+    shared memory."""
+    g = np.random.default_rng(31 + P)
+    pts = g.standard_normal((n, 3))
     pts *= (g.random(len(pts)) ** (1 / 3) * 1.5 / np.linalg.norm(pts, axis=1))[:, None]
     (dp,) = to_dev(pts)
-    P, Rs = 12, 1.5
+    Rs = 1.5
     B64 = hs().basis(dp, P, Rs, precision="fp64")
     Bdf = hs().basis(dp, P, Rs, precision="fp32")
     rho = np.linalg.norm(pts, axis=1) / Rs

@@ -179,8 +179,10 @@ int hsma_plan_set_inset_skin(hsma_plan_t plan, double skin);
  * left (on = 0, the default, faster alone).  CTAs that finish their item
  * free their SM, so work on a stream of higher priority (another plan, a
  * serving lane) starts between items instead of after the whole step; the
+ * items are cut 8x finer than the tuned granularity, so an SM frees up
+ * sooner, at the cost of more partial records in the workspace; the
  * tensor-core fit then also uses a quarter of the SMs.  Results are the
- * same up to the fit's grouping of sums.  No counterpart in the paper. */
+ * same up to the grouping of the sums.  No counterpart in the paper. */
 int hsma_plan_set_preemptible(hsma_plan_t plan, int on);
 
 /* Counts of the plan's single-system steps since creation: in-set lists

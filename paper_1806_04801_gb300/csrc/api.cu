@@ -249,6 +249,8 @@ int ensure_pinned(hsma_plan_s *p, size_t bytes)
 // resident at once, which a smaller grid finds sooner beside other work).
 int fit_ctas(const hsma_plan_s *p) { return p->preemptible ? std::max(8, p->num_sms / 4) : p->num_sms; }
 
+constexpr int kPreemptibleItemsFactor = 8;  // work items of a preemptible plan per tuned item
+
 // Work decomposition of a batch: targets per block, source chunks per system,
 // work items, surface blocks.  Pure host arithmetic.
 int tuned_ctas(const hsma_plan_s *p, int precision, int variant)
@@ -311,7 +313,10 @@ void shape_batch(const hsma_plan_s *p, int nsys, const long long *n, int precisi
         int ntb = (int)((n[s] + TB - 1) / TB) + ntb_mon;
         work += (double)ntb * ns_est[s];
     }
-    const double items_wanted = (double)std::max(1, tu.items_per_slot) * slots;
+    // preemptible plans cut their items finer, so that an SM frees up (for a
+    // higher-priority stream) after a shorter wait
+    const double items_wanted =
+        (double)std::max(1, tu.items_per_slot) * slots * (p->preemptible ? kPreemptibleItemsFactor : 1);
     const double chunk = std::max(4.0 * tile, work / items_wanted);
     long long part = 0, src = 0, tgt = 0, rec = 0, cnt = 0, hist = 0, tiles = 0, max_tiles = 0;
     long long items = 0, surf = 0;

@@ -244,9 +244,10 @@ __device__ __forceinline__ float2 df_of(double v)
 // in the binade underneath, whose spacing is half as large, so lo is counted
 // in those units.  A hi below 2^-74 (that is, below 2^-74 of the point's
 // scale: the kernel scales every point to a largest coordinate in [1, 2))
-// gives a signed zero.  kChecked adds the range checks for exponent offsets
-// that can leave FP64's normal range (result zero below it, infinity above);
-// points of ordinary size never need them.
+// gives a signed zero.  kChecked adds the checks for exponent offsets that
+// can leave FP64's normal range (result zero below it, infinity above) and
+// for a non-finite hi (result NaN); finite points of ordinary size never
+// need them.
 template <bool kChecked>
 __device__ __forceinline__ double df_to_f64_scaled(float2 v, uint32_t kb, int k)
 {
@@ -266,6 +267,7 @@ __device__ __forceinline__ double df_to_f64_scaled(float2 v, uint32_t kb, int k)
         const int ed = (int)eh + 896 + k;
         if (ed <= 0) bits = (unsigned long long)sign << 32;
         if (ed >= 2047) bits = (unsigned long long)(sign | 0x7ff00000u) << 32;
+        if (eh == 255u) bits = (unsigned long long)(sign | 0x7ff80000u) << 32;
     }
     return __longlong_as_double((long long)bits);
 }
@@ -475,8 +477,10 @@ __global__ void __launch_bounds__(32 * kBasisDfWarps) basis_df_kernel(const __gr
         }
         const float2 X = df_of(px * f), Y = df_of(py * f), Z = df_of(pz * f);
         const float2 R2 = df_add_df(df_add_df(df_mul(X, X), df_mul(Y, Y)), df_mul(Z, Z));
-        // exponent offsets e n with n <= P stay inside FP64's range for every value of FP32 size
-        const bool plain = __all_sync(0xffffffffu, abs(e) * P <= 895);
+        // exponent offsets e n with n <= P stay inside FP64's range for every
+        // value of FP32 size, and a finite point gives finite values
+        const bool finite = isfinite(px) && isfinite(py) && isfinite(pz);
+        const bool plain = __all_sync(0xffffffffu, finite && abs(e) * P <= 895);
         if (plain)
             basis_df_rows<false>(P, ta, tb, td, te, w, lane, X, Y, Z, R2, e, rows, out + i0 * ld, (int)ld);
         else

@@ -168,6 +168,23 @@ def test_basis_entry_point(precision, P):
     assert B[777, 0] == pytest.approx(1.0 / np.sqrt(4 * np.pi), rel=1e-15) and np.all(B[777, 1:] == 0.0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_basis_of_a_non_finite_point_is_nan(precision):
+    """A point with NaN coordinates between finite ones: Y_00 (which does not
+    depend on the point) and NaN everywhere else in its row, the other rows
+    as for finite input."""
+    pts = _basis_points()[:100].copy()
+    pts[37] = np.nan
+    (dp,) = to_dev(pts)
+    P, Rs = 12, 1.7
+    B = hs().basis(dp, P, Rs, precision=precision).cpu().numpy()
+    assert B[37, 0] == pytest.approx(1.0 / np.sqrt(4 * np.pi), rel=1e-15)
+    assert np.all(np.isnan(B[37, 1:]))
+    rows = np.delete(np.arange(100), 37)
+    ref, scale = _basis_reference(pts[rows], P, Rs)
+    assert np.all(np.abs(B[rows] - ref) <= BASIS_TOL[precision] * scale + 1e-300)
+
+
 @pytest.mark.parametrize("P,n", [(12, 200_003), (40, 40_001)])
 def test_basis_double_float_and_fp64_agree_at_scale(P, n):
     """The two forms at many points spread over the Rs ball (the plan's use:

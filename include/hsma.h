@@ -457,7 +457,9 @@ int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const dou
  * normalised, in double-float arithmetic (pairs of FP32 words) on the FP32
  * pipe, several times faster on this part and accurate to ~1e-14 of that
  * scale.  Each point is scaled by a power of two first, so neither form
- * underflows for points near the origin.  Returns once out holds the basis.
+ * underflows for points near the origin.  A point with a non-finite
+ * coordinate gets non-finite values (NaN or infinity) wherever they depend
+ * on it.  Allocates no device memory.  Returns once out holds the basis.
  * Errors: HSMA_E_ARG (p, Rs, np, null pointers, precision), HSMA_E_CUDA. */
 int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, int precision, void *stream);
 

@@ -449,19 +449,11 @@ int ensure_workspace(hsma_plan_s *p, size_t bytes)
     return HSMA_OK;
 }
 
-double host_norm(int n, int m)
-{
-    // sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!)
-    double r = 1.0;
-    for (int t = n - m + 1; t <= n + m; ++t) r /= (double)t;
-    return sqrt((m == 0 ? 1.0 : 2.0) * (2.0 * n + 1.0) / (4.0 * kPi) * r);
-}
-
 std::vector<double> norm_table(int P)
 {
     std::vector<double> v((P + 1) * (P + 1));
     for (int n = 0; n <= P; ++n)
-        for (int m = -n; m <= n; ++m) v[n * n + n + m] = host_norm(n, abs(m));
+        for (int m = -n; m <= n; ++m) v[n * n + n + m] = basis_norm(n, abs(m));
     return v;
 }
 
@@ -1392,14 +1384,14 @@ int hsma_plan(hsma_plan_t *out, const double box[3], int bc, int p, double R, in
         }
         if (rc) break;
         // basis at the monitoring targets (stride 4 doubles per point)
-        if ((rc = launch_basis(p, R, nmon, (const double *)pl->mon64, 4, pl->norm, Bx, Nb, st))) break;
+        if ((rc = launch_basis(p, R, nmon, (const double *)pl->mon64, 4, Bx, Nb, st))) break;
         const double *Bxt = (bc == HSMA_BC_PERIODIC) ? Bx + (size_t)K * Nb : nullptr;
         if ((rc = launch_fitting_matrix(K, Nb, ncols, bc == HSMA_BC_PERIODIC ? 1 : 0, Bx, Bxt, Mcol, pl->Mrow, st)))
             break;
         if ((rc = build_pseudo_inverse(K, ncols, Mcol, pl->Mp, &cond, &rank_ok, st))) break;
         if ((rc = launch_quadrature(F2, F1, R, pl->dirs, st))) break;
         // basis at Rs u_j == basis of the unit vector u_j with unit radius
-        if ((rc = launch_basis(p, 1.0, ndir, (const double *)pl->dirs, 4, pl->norm, pl->Bq, Nb, st))) break;
+        if ((rc = launch_basis(p, 1.0, ndir, (const double *)pl->dirs, 4, pl->Bq, Nb, st))) break;
         if ((rc = prepare_tc_operands(K, ncols, pl->Mp, pl->Mrow, pl->tc_hi, pl->tc_lo, pl->tc_mdf, st))) break;
         if ((rc = sort_monitor_targets(pl, st))) break;
         if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -1960,23 +1952,11 @@ int hsma_basis(int p, double Rs, int64_t np, const double *pts, double *out, int
 {
     if (p < 0 || p > 40 || !(Rs > 0) || np < 1 || !pts || !out) return HSMA_E_ARG;
     if (precision != HSMA_FP64 && precision != HSMA_FP32_ACC64) return HSMA_E_ARG;
-    int Nb = (p + 1) * (p + 1);
-    if (precision == HSMA_FP32_ACC64) {
-        cudaStream_t st = (cudaStream_t)stream;
-        int rc = launch_basis_df(p, Rs, np, pts, 3, out, Nb, st);
-        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
-        return rc;
-    }
-    auto nt = norm_table(p);
-    double *dn = nullptr;
+    const int Nb = (p + 1) * (p + 1);
     cudaStream_t st = (cudaStream_t)stream;
-    HSMA_CUDA_TRY(dev_malloc(&dn, sizeof(double) * Nb));
-    int rc = HSMA_OK;
-    if (cudaMemcpyAsync(dn, nt.data(), sizeof(double) * Nb, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        rc = HSMA_E_CUDA;
-    if (!rc) rc = launch_basis(p, Rs, np, pts, 3, dn, out, Nb, st);
+    int rc = precision == HSMA_FP32_ACC64 ? launch_basis_df(p, Rs, np, pts, 3, out, Nb, st)
+                                          : launch_basis(p, Rs, np, pts, 3, out, Nb, st);
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = HSMA_E_CUDA;
-    dev_free(dn);
     return rc;
 }
 

@@ -294,8 +294,11 @@ int launch_monitor_sphere(int K, double R0, const double L[3], double4_32a *out6
 int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *out64, float4 *hi, float4 *lo,
                          cudaStream_t st);
 int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st);
-int launch_basis(int P, double Rs, long long np, const double *pts, int pts_stride, const double *norm,
-                 double *out, long long ld, cudaStream_t st);
+// orthonormalisation constant of the real solid harmonic (n, m), m >= 0:
+// sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!)
+double basis_norm(int n, int m);
+int launch_basis(int P, double Rs, long long np, const double *pts, int pts_stride, double *out, long long ld,
+                 cudaStream_t st);
 // the same basis in double-float arithmetic on the FP32 pipe (no norm table)
 int launch_basis_df(int P, double Rs, long long np, const double *pts, int pts_stride, double *out, long long ld,
                     cudaStream_t st);

@@ -122,16 +122,33 @@ constexpr int kBasisMaxP = 40;
 constexpr int kBasisThreads = 128;
 constexpr double kBasisRowsInFlightBytes = 24.0 * 1024 * 1024;
 
-__global__ void __launch_bounds__(kBasisThreads) basis_kernel(int P, double inv_rs, long long np,
+// The normalisation constants of every n, m <= kBasisMaxP at k = n^2 + n + m,
+// computed once on the host and passed by value (no device buffer).
+struct BasisNormTable {
+    double v[(kBasisMaxP + 1) * (kBasisMaxP + 1)];
+};
+
+const BasisNormTable &basis_norm_table()
+{
+    static const BasisNormTable t = [] {
+        BasisNormTable v{};
+        for (int n = 0; n <= kBasisMaxP; ++n)
+            for (int m = -n; m <= n; ++m) v.v[n * n + n + m] = basis_norm(n, m < 0 ? -m : m);
+        return v;
+    }();
+    return t;
+}
+
+__global__ void __launch_bounds__(kBasisThreads) basis_kernel(const __grid_constant__ BasisNormTable norm_t, int P,
+                                                              double inv_rs, long long np,
                                                               const double *__restrict__ pts, int stride,
-                                                              const double *__restrict__ norm_g,
                                                               double *__restrict__ out, long long ld)
 {
     extern __shared__ double bsm[];  // [P + 1] reciprocals, then [(P + 1)^2] normalisation
     double *rinv = bsm, *norm = bsm + (P + 1);
     const int Nb = (P + 1) * (P + 1);
     for (int k = threadIdx.x; k <= P; k += blockDim.x) rinv[k] = k > 0 ? 1.0 / (double)k : 0.0;
-    for (int k = threadIdx.x; k < Nb; k += blockDim.x) norm[k] = norm_g[k];
+    for (int k = threadIdx.x; k < Nb; k += blockDim.x) norm[k] = norm_t.v[k];
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
          i += (long long)gridDim.x * blockDim.x) {
@@ -654,6 +671,14 @@ int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *o64, 
     return HSMA_OK;
 }
 
+double basis_norm(int n, int m)
+{
+    // sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!), m >= 0
+    double r = 1.0;
+    for (int t = n - m + 1; t <= n + m; ++t) r /= (double)t;
+    return std::sqrt((m == 0 ? 1.0 : 2.0) * (2.0 * n + 1.0) / (4.0 * kPi) * r);
+}
+
 int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st)
 {
     quadrature_kernel<<<(F2 + 1 + 127) / 128, 128, 0, st>>>(F2, F1, Rs, dirs);
@@ -662,8 +687,8 @@ int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t
     return HSMA_OK;
 }
 
-int launch_basis(int P, double Rs, long long np, const double *pts, int stride, const double *norm, double *out,
-                 long long ld, cudaStream_t st)
+int launch_basis(int P, double Rs, long long np, const double *pts, int stride, double *out, long long ld,
+                 cudaStream_t st)
 {
     if (np <= 0) return HSMA_OK;
     if (P < 0 || P > kBasisMaxP) return HSMA_E_ARG;
@@ -675,7 +700,8 @@ int launch_basis(int P, double Rs, long long np, const double *pts, int stride, 
         std::max<long long>(sms, (long long)(kBasisRowsInFlightBytes / row_bytes) / kBasisThreads);
     const long long blocks = std::min<long long>((np + kBasisThreads - 1) / kBasisThreads, in_flight);
     const size_t smem = sizeof(double) * ((size_t)(P + 1) + (size_t)(P + 1) * (P + 1));
-    basis_kernel<<<(unsigned)blocks, kBasisThreads, smem, st>>>(P, 1.0 / Rs, np, pts, stride, norm, out, ld);
+    basis_kernel<<<(unsigned)blocks, kBasisThreads, smem, st>>>(basis_norm_table(), P, 1.0 / Rs, np, pts, stride,
+                                                                 out, ld);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

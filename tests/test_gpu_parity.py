@@ -158,7 +158,9 @@ def test_basis_entry_point(precision, P):
     pts = _basis_points()
     Rs = 1.7
     (dp,) = to_dev(pts)
+    allocs = hs().allocation_calls()
     B = hs().basis(dp, P, Rs, precision=precision).cpu().numpy()
+    assert hs().allocation_calls() == allocs  # both forms take their tables by value: no device buffer
     ref, scale = _basis_reference(pts, P, Rs)
     assert np.all(np.isfinite(B))
     err = np.abs(B - ref)

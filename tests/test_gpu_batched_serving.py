@@ -223,8 +223,9 @@ def test_serving_cancellation():
 
 def test_preemptible_pair_work_gives_the_same_results():
     """One CTA per work item (the serving bulk lanes' mode) against the
-    persistent grid: the same items and the same fixed-order reduction, so
-    the FP32 pair sums with the FP64 fit are bit-identical."""
+    persistent grid.  These systems are small enough that both modes take the
+    smallest chunk (four tiles), so the items and the fixed-order reduction
+    are the same and the FP32 pair sums with the FP64 fit are bit-identical."""
     w = I.BATCH_PERIODIC
     systems = [I.uniform_pm1(int(n), w.box, seed_offset=140 + i) for i, n in enumerate([900, 5000, 20000])]
     xyz = np.concatenate([s[0] for s in systems])
@@ -242,6 +243,24 @@ def test_preemptible_pair_work_gives_the_same_results():
         E1, F1, _, _ = plan.energy_forces_batched(dx, dq, off)
         for i in range(len(systems)):
             assert rel_energy_err(E1[i], E0[i], systems[i][1]) <= 1e-7
+
+
+def test_preemptible_pair_work_on_finer_items():
+    """At 1e5 charges the preemptible mode cuts its items 8x finer than the
+    persistent grid's, so the same pair sums are grouped differently: equal
+    up to summation order (measured: energy identical, forces within 2e-11 of
+    the RMS force)."""
+    w = I.LARGE_PERIODIC
+    xyz, q = I.large_periodic(100_000)
+    dx, dq = to_dev(xyz, q)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        plan.set_tuning(17, 48)
+        U0, F0, _, _ = plan.energy_forces(dx, dq)
+        plan.set_preemptible(True)
+        U1, F1, _, _ = plan.energy_forces(dx, dq)
+    F0, F1 = F0.cpu().numpy(), F1.cpu().numpy()
+    assert abs(U1 - U0) <= 1e-12 * abs(U0)
+    assert np.abs(F1 - F0).max() <= 1e-9 * np.sqrt(np.mean(F0 ** 2))
 
 
 def test_small_request_overtakes_a_large_batch():

@@ -466,12 +466,18 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
         lat, slow, nn = np.array(lat), np.array(slow), np.array(nn)
         small = nn <= express_max_n
         pct = lambda a, p: float(np.percentile(a, p)) if len(a) else None  # noqa: E731
+        by_size = {}
+        for name, lo, hi in (("le20k", 0, 20000), ("20k_60k", 20000, 60000), ("gt60k", 60000, np.inf)):
+            m = (nn > lo) & (nn <= hi)
+            by_size[name] = {"count": int(m.sum()), "p99_ms": pct(lat[m], 99), "slowdown_p50": pct(slow[m], 50),
+                             "slowdown_p99": pct(slow[m], 99)}
         return {"rate_hz": rate, "requests": count, "completed": int(len(lat)),
                 "systems_per_s": len(lat) / wall, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                 "slowdown_p50": pct(slow, 50), "slowdown_p99": pct(slow, 99),
                 "small": {"count": int(small.sum()), "p50_ms": pct(lat[small], 50), "p99_ms": pct(lat[small], 99)},
                 "large": {"count": int((~small).sum()), "p50_ms": pct(lat[~small], 50),
                           "p99_ms": pct(lat[~small], 99)},
+                "by_size": by_size,
                 "mean_batch": float(np.mean(batch)), "wall_s": wall, "hbm_budget_bytes": int(st["hbm_budget_bytes"])}
 
     main = replay(rate_hz, n_requests, 0)

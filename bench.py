@@ -397,13 +397,14 @@ def run_grounded(steps: int, warmup: int):
 
 
 # ------------------------------------------------------- serving workload
-def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, lanes: int = 3, max_batch: int = 32,
-                express_lanes: int = 1, express_max_n: int = 20000):
+def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, lanes: int = 4, max_batch: int = 32,
+                express_lanes: int = 1, express_max_n: int = 20000, mid_lanes: int = 1, mid_max_n: int = 60000):
     """Poisson stream of periodic boxes with N log-uniform in [1000, 200000]:
     requests are submitted at their arrival times to the continuous-batching
     server; latency is submit -> result.  One express lane (high-priority
-    stream) serves requests of at most express_max_n particles, the bulk
-    lanes the rest with preemptible pair work.  Besides p50/p99 of the
+    stream) serves requests of at most express_max_n particles, one medium
+    lane (middle priority, preemptible pair work) those up to mid_max_n, the
+    bulk lanes the rest with preemptible pair work.  Besides p50/p99 of the
     latency, each request's slowdown -- its latency over the time the same
     request takes alone through a plan with host buffers -- is reported:
     with N spanning 200x the latency percentiles mostly restate the size
@@ -435,7 +436,8 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
         t_arr, sizes = I.poisson_trace(count, rate_hz=rate, seed_offset=4 + seed)
         reqs = [I.uniform_pm1(int(n), w.box, seed_offset=5000 + seed * 1000 + i) for i, n in enumerate(sizes)]
         with hsma.Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32_tc", lanes=lanes,
-                         max_batch=max_batch, express_lanes=express_lanes, express_max_n=express_max_n) as srv:
+                         max_batch=max_batch, express_lanes=express_lanes, express_max_n=express_max_n,
+                         mid_lanes=mid_lanes, mid_max_n=mid_max_n) as srv:
             # warm the lanes (plans, workspaces): a small and a large request each
             for _ in range(lanes):
                 for r in (reqs[int(np.argmin(sizes))], reqs[int(np.argmax(sizes))]):
@@ -482,7 +484,8 @@ def run_serving(n_requests: int, rate_hz: float = 2000.0, sweep: bool = True, la
 
     main = replay(rate_hz, n_requests, 0)
     out = {"workload": "serving-periodic-p10 (Poisson arrivals, N log-uniform in [1000, 200000], +-1)",
-           "lanes": lanes, "express_lanes": express_lanes, "express_max_n": express_max_n, "max_batch": max_batch,
+           "lanes": lanes, "express_lanes": express_lanes, "express_max_n": express_max_n, "mid_lanes": mid_lanes,
+           "mid_max_n": mid_max_n, "max_batch": max_batch,
            "alone_ms": dict(zip(map(str, sizes_ref), alone)), "offered": main}
     if sweep:
         cap = main["systems_per_s"]

@@ -346,8 +346,11 @@ int hsma_plan_load_tuning(hsma_plan_t plan, const char *cache_path);
  * apart and have lanes of their own on a high-priority stream, while the
  * bulk lanes' pair work is preemptible (hsma_plan_set_preemptible), so a
  * small request waits for work items of a large batch, not for the whole
- * batch.  Thread-safe: submit and result may be called from any host
- * thread. */
+ * batch.  Optional medium lanes (mid_lanes) do the same one level down:
+ * medium requests wait for work items of large batches, small ones for work
+ * items of medium and large ones.  A batch holds the oldest waiting request
+ * of its class and the waiting ones within a factor 4 of its size.
+ * Thread-safe: submit and result may be called from any host thread. */
 typedef struct hsma_server_s *hsma_server_t;
 
 typedef struct {
@@ -362,6 +365,13 @@ typedef struct {
                                  work; an express lane's workspace is allocated at
                                  creation for max_batch requests of express_max_n   */
     int64_t express_max_n;    /* requests with n <= this are small (default 20000)     */
+    int mid_lanes;            /* lanes that serve only medium requests (express_max_n <
+                                 n <= mid_max_n), on a stream of middle priority, with
+                                 preemptible pair work and a workspace allocated at
+                                 creation for max_batch requests of mid_max_n;
+                                 express_lanes + mid_lanes < lanes (default 0: medium
+                                 requests are large ones)                            */
+    int64_t mid_max_n;        /* upper size of a medium request (>= express_max_n)    */
 } hsma_server_opts;
 
 typedef struct {

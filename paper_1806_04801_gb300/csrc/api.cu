@@ -1169,12 +1169,18 @@ int hsma::plan_reserve(hsma_plan_t p, int nsys, long long n_each)
 {
     if (!p || nsys < 1 || nsys > kMaxSystems || n_each < 1 || n_each > kMaxInsetSlots / p->nshifts)
         return HSMA_E_ARG;
-    std::vector<long long> n(nsys, n_each);
-    BatchShape sh;
-    shape_batch(p, nsys, n.data(), p->precision, choose_tuning(p, nsys, n.data()), &sh);
-    if (sh.items < 0 || sh.surf_items < 0) return HSMA_E_ARG;
-    Workspace w;
-    int rc = ensure_workspace(p, carve_workspace(p, sh, p->precision, true, true, nullptr, &w));
+    // the largest workspace over the batch and the single request of that
+    // size: they take different tunings (and so tiles and work items)
+    size_t need = 0;
+    for (int k : {1, nsys}) {
+        std::vector<long long> n(k, n_each);
+        BatchShape sh;
+        shape_batch(p, k, n.data(), p->precision, choose_tuning(p, k, n.data()), &sh);
+        if (sh.items < 0 || sh.surf_items < 0) return HSMA_E_ARG;
+        Workspace w;
+        need = std::max(need, carve_workspace(p, sh, p->precision, true, true, nullptr, &w));
+    }
+    int rc = ensure_workspace(p, need);
     if (rc) return rc;
     const size_t pin_bytes = align_up(sizeof(SysDesc) * nsys, 64) + align_up(sizeof(double) * nsys, 64) +
                              align_up(sizeof(long long) * nsys, 64) + align_up(sizeof(int) * nsys, 64);

@@ -17,7 +17,10 @@
 // stream of lowest priority, with their pair work launched as one CTA per
 // work item (hsma_plan_set_preemptible): as bulk CTAs finish their items the
 // SMs go to the express lanes' pending work, so a small request waits for
-// work items of a large batch, not for the whole batch.  Each system's arithmetic depends only on its own inputs
+// work items of a large batch, not for the whole batch.  Optional medium
+// lanes sit between the two: medium requests (express_max_n < n <=
+// mid_max_n) on a stream of middle priority, with preemptible pair work and
+// a workspace reserved at creation like the express lanes'.  Each system's arithmetic depends only on its own inputs
 // and on how its sources are split into chunks, so a result is the same,
 // within rounding of the chunk grouping, alone or in a mix.
 #include <string.h>
@@ -59,7 +62,7 @@ struct hsma_server_s {
     std::vector<size_t> held;  // device bytes each lane holds for its current batch
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
-    std::deque<Request *> queue, queue_small;  // large / small requests, oldest first
+    std::deque<Request *> queue, queue_small, queue_mid;  // large / small / medium requests, oldest first
     std::unordered_map<int64_t, Request *> all;
     int64_t next_id = 1;
     bool stop = false;
@@ -71,11 +74,14 @@ struct hsma_server_s {
 
 namespace {
 
+constexpr long long kBatchSizeRatio = 4;  // largest / smallest request size within one batch
+
 void lane_main(hsma_server_s *s, int lane)
 {
     cudaSetDevice(s->device);
     hsma_plan_t plan = s->plans[lane];
     const bool express = lane < s->opts.express_lanes;
+    const bool mid = !express && lane < s->opts.express_lanes + s->opts.mid_lanes;
     std::vector<int64_t> offsets;
     std::vector<double> xyz, q, energies, forces;
     std::vector<int> status;
@@ -86,6 +92,7 @@ void lane_main(hsma_server_s *s, int lane)
     const bool bulk_takes_small = s->opts.express_lanes == 0;
     auto pick = [&]() -> std::deque<Request *> * {
         if (express) return s->queue_small.empty() ? nullptr : &s->queue_small;
+        if (mid) return s->queue_mid.empty() ? nullptr : &s->queue_mid;
         if (!s->queue.empty()) return &s->queue;
         return (bulk_takes_small && !s->queue_small.empty()) ? &s->queue_small : nullptr;
     };
@@ -100,12 +107,17 @@ void lane_main(hsma_server_s *s, int lane)
             for (size_t l = 0; l < s->held.size(); ++l)
                 if ((int)l != lane) others += s->held[l];
             size_t used = 0;
-            while (!qu->empty() && (int)batch.size() < s->opts.max_batch) {
-                Request *r = qu->front();
+            // the oldest request, then the waiting ones within a factor
+            // kBatchSizeRatio of its size: a request batched with much larger
+            // ones would finish only when they do; the others stay queued, in
+            // order, for the next free lane
+            long long n_first = 0;
+            for (size_t i = 0; i < qu->size() && (int)batch.size() < s->opts.max_batch;) {
+                Request *r = (*qu)[i];
                 size_t one = 0;
                 hsma_plan_footprint(plan, r->n, &one);
                 if (one > s->opts.hbm_budget_bytes) {  // can never run
-                    qu->pop_front();
+                    qu->erase(qu->begin() + (std::ptrdiff_t)i);
                     r->status = HSMA_E_CAPACITY;
                     r->t_done = Clock::now();
                     r->t_start = r->t_done;
@@ -113,8 +125,13 @@ void lane_main(hsma_server_s *s, int lane)
                     s->cv_done.notify_all();
                     continue;
                 }
+                if (!batch.empty() && (r->n > kBatchSizeRatio * n_first || kBatchSizeRatio * r->n < n_first)) {
+                    ++i;  // another size class: leave it for the next lane
+                    continue;
+                }
                 if (others + used + one > s->opts.hbm_budget_bytes) break;  // wait for memory
-                qu->pop_front();
+                qu->erase(qu->begin() + (std::ptrdiff_t)i);
+                if (batch.empty()) n_first = r->n;
                 used += one;
                 batch.push_back(r);
             }
@@ -150,9 +167,9 @@ void lane_main(hsma_server_s *s, int lane)
             std::lock_guard<std::mutex> lk(s->mu);
             s->held[lane] = 0;
             // keep a bulk lane's cached workspace within what the budget leaves
-            // (express lanes keep the workspace reserved at creation: freeing
-            // and growing it would synchronise the device behind bulk work)
-            if (!express) {
+            // (express and medium lanes keep the workspace reserved at creation:
+            // freeing and growing it would synchronise the device behind bulk work)
+            if (!express && !mid) {
                 size_t others_now = 0;
                 for (size_t l = 0; l < s->held.size(); ++l) others_now += s->held[l];
                 size_t room = s->opts.hbm_budget_bytes > others_now ? s->opts.hbm_budget_bytes - others_now : 0;
@@ -199,6 +216,8 @@ int hsma_server_opts_default(hsma_server_opts *o)
     o->precision = HSMA_FP32_ACC64;
     o->express_lanes = 1;
     o->express_max_n = 20000;
+    o->mid_lanes = 0;
+    o->mid_max_n = 60000;
     return HSMA_OK;
 }
 
@@ -211,7 +230,9 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
     hsma_server_opts_default(&o);
     if (opts) o = *opts;
     if (o.lanes < 1 || o.lanes > 16 || o.max_batch < 1 || o.max_batch > 65528) return HSMA_E_ARG;
-    if (o.express_lanes < 0 || (o.express_lanes > 0 && o.express_lanes >= o.lanes) || o.express_max_n < 0)
+    if (o.express_lanes < 0 || o.mid_lanes < 0 || o.express_max_n < 0 ||
+        (o.express_lanes + o.mid_lanes > 0 && o.express_lanes + o.mid_lanes >= o.lanes) ||
+        (o.mid_lanes > 0 && o.mid_max_n < o.express_max_n))
         return HSMA_E_ARG;  // at least one bulk lane serves the large requests
     if (o.hbm_budget_bytes == 0) {
         size_t free_b = 0, total_b = 0;
@@ -233,10 +254,14 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
         delete s;
         return HSMA_E_CUDA;
     }
+    // numerically between the two (the same as the highest when the range has no middle)
+    const int prio_mid = prio_low - prio_high >= 2 ? (prio_high + prio_low) / 2 : prio_high;
     for (int l = 0; l < o.lanes; ++l) {
         const bool express = l < o.express_lanes;
+        const bool mid = !express && l < o.express_lanes + o.mid_lanes;
         cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, express ? prio_high : prio_low) != cudaSuccess) {
+        const int prio = express ? prio_high : (mid ? prio_mid : prio_low);
+        if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess) {
             hsma_server_destroy(s);
             return HSMA_E_CUDA;
         }
@@ -245,16 +270,43 @@ int hsma_server_create(hsma_server_t *out, const double box[3], int bc, int p, d
         hsma_plan_t pl = nullptr;
         int rc = hsma_plan(&pl, box, bc, p, R, Q, Kmon, &po);
         if (!rc && !express) rc = hsma_plan_set_preemptible(pl, 1);
-        // an express lane never allocates while serving: its workspace holds
-        // a full batch of the largest small requests from the start
+        // express and medium lanes never allocate while serving: their
+        // workspace holds a full batch of the largest requests of their class
+        // from the start (reserved after the preemptible setting, which sets
+        // the number of partial records)
         if (!rc && express && o.express_max_n > 0)
             rc = hsma::plan_reserve(pl, o.max_batch, o.express_max_n);
+        if (!rc && mid) rc = hsma::plan_reserve(pl, o.max_batch, o.mid_max_n);
         if (rc) {
             if (pl) hsma_plan_destroy(pl);
             hsma_server_destroy(s);
             return rc;
         }
         s->plans.push_back(pl);
+    }
+    // One- and two-system steps of a few charges on every lane before serving:
+    // the CUDA runtime loads a kernel at its first launch, and a load can wait
+    // for the work already on the device -- a lane's first request would
+    // otherwise queue behind a large batch on another lane.
+    {
+        const int nw = 8;
+        std::vector<double> wx(3 * 2 * nw), wq(2 * nw), we(2), wf(3 * 2 * nw);
+        std::vector<int> ws(2);
+        for (int i = 0; i < 2 * nw; ++i) {
+            for (int a = 0; a < 3; ++a) wx[3 * i + a] = box[a] * (0.3 + 0.4 * (double)((i >> a) & 1) + 0.01 * i);
+            wq[i] = (i & 1) ? -1.0 : 1.0;
+        }
+        for (int l = 0; l < o.lanes; ++l) {
+            for (int k = 1; k <= 2; ++k) {
+                const int64_t off[3] = {0, nw, 2 * nw};
+                hsma_particles in{(int64_t)k * nw, wx.data(), wq.data(), 0};
+                int rc = hsma_energy_forces_batched(s->plans[l], k, off, &in, we.data(), wf.data(), nullptr, ws.data());
+                if (rc) {
+                    hsma_server_destroy(s);
+                    return rc;
+                }
+            }
+        }
     }
     s->held.assign(o.lanes, 0);
     for (int l = 0; l < o.lanes; ++l) s->threads.emplace_back(lane_main, s, l);
@@ -282,7 +334,12 @@ int hsma_server_submit(hsma_server_t s, int64_t n, const double *xyz, const doub
             s->t0_set = true;
         }
         s->all[r->id] = r;
-        (n <= s->opts.express_max_n ? s->queue_small : s->queue).push_back(r);
+        if (n <= s->opts.express_max_n)
+            s->queue_small.push_back(r);
+        else if (s->opts.mid_lanes > 0 && n <= s->opts.mid_max_n)
+            s->queue_mid.push_back(r);
+        else
+            s->queue.push_back(r);
         *ticket = r->id;
     }
     s->cv_work.notify_all();
@@ -323,7 +380,7 @@ int hsma_server_cancel(hsma_server_t s, int64_t ticket)
     auto it = s->all.find(ticket);
     if (it == s->all.end()) return HSMA_E_NOT_FOUND;
     Request *r = it->second;
-    for (auto *qu : {&s->queue, &s->queue_small})
+    for (auto *qu : {&s->queue, &s->queue_small, &s->queue_mid})
         for (auto q = qu->begin(); q != qu->end(); ++q)
             if (*q == r) {
                 qu->erase(q);
@@ -344,7 +401,7 @@ int hsma_server_stats(hsma_server_t s, hsma_server_stats_t *st)
     st->completed = s->completed;
     st->failed = s->failed;
     st->cancelled = s->cancelled;
-    st->queued = (int64_t)(s->queue.size() + s->queue_small.size());
+    st->queued = (int64_t)(s->queue.size() + s->queue_small.size() + s->queue_mid.size());
     st->batches = s->batches;
     st->mean_batch = s->batches ? (double)s->batched_systems / s->batches : 0.0;
     st->elapsed_s = s->t0_set ? std::chrono::duration<double>(s->t_last_done - s->t0).count() : 0.0;

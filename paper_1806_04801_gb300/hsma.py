@@ -553,7 +553,8 @@ def basis(pts, p: int, Rs: float, precision: str = "fp64", stream=None):
 class hsma_server_opts(ctypes.Structure):
     """Mirror of hsma_server_opts (include/hsma.h)."""
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("lanes", ctypes.c_int),
-                ("precision", ctypes.c_int), ("express_lanes", ctypes.c_int), ("express_max_n", ctypes.c_int64)]
+                ("precision", ctypes.c_int), ("express_lanes", ctypes.c_int), ("express_max_n", ctypes.c_int64),
+                ("mid_lanes", ctypes.c_int), ("mid_max_n", ctypes.c_int64)]
 
 
 class hsma_request_info(ctypes.Structure):
@@ -587,7 +588,7 @@ class Server:
 
     def __init__(self, box, bc: int, p: int, R: float, Q: int, Kmon: int, precision=FP32_ACC64, lanes: int = 2,
                  max_batch: int = 64, hbm_budget_bytes: int = 0, express_lanes: int | None = None,
-                 express_max_n: int | None = None):
+                 express_max_n: int | None = None, mid_lanes: int = 0, mid_max_n: int | None = None):
         L = _lib()
         o = hsma_server_opts()
         _check(L.hsma_server_opts_default(ctypes.byref(o)), "hsma_server_opts_default")
@@ -601,6 +602,9 @@ class Server:
             o.express_lanes = min(int(o.express_lanes), int(lanes) - 1)
         if express_max_n is not None:
             o.express_max_n = int(express_max_n)
+        o.mid_lanes = int(mid_lanes)
+        if mid_max_n is not None:
+            o.mid_max_n = int(mid_max_n)
         box_arr = (ctypes.c_double * 3)(*[float(b) for b in box])
         h = ctypes.c_void_p()
         _check(L.hsma_server_create(ctypes.byref(h), box_arr, int(bc), int(p), float(R), int(Q), int(Kmon),

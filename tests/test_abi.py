@@ -162,10 +162,14 @@ def test_argument_errors_are_caught_before_any_device_work(lib):
     assert lib.hsma_server_opts_default(ctypes.byref(so)) == 0
     assert so.max_batch == 64 and so.lanes == 2 and so.precision == hsma.FP32_ACC64
     srv = ctypes.c_void_p()
-    for field, bad in (("lanes", 0), ("lanes", 17), ("max_batch", 0), ("max_batch", 65529)):
+    assert so.mid_lanes == 0 and so.mid_max_n >= so.express_max_n
+    for changes in ({"lanes": 0}, {"lanes": 17}, {"max_batch": 0}, {"max_batch": 65529}, {"mid_lanes": -1},
+                    {"lanes": 2, "express_lanes": 1, "mid_lanes": 1},     # no bulk lane left
+                    {"lanes": 3, "mid_lanes": 1, "mid_max_n": 1000}):     # medium below small
         o2 = hsma.hsma_server_opts()
         lib.hsma_server_opts_default(ctypes.byref(o2))
-        setattr(o2, field, bad)
+        for field, bad in changes.items():
+            setattr(o2, field, bad)
         assert lib.hsma_server_create(ctypes.byref(srv), unit, 0, 8, 1.5, 2000, 600, ctypes.byref(o2)) == ARG
     assert srv.value is None
     t = ctypes.c_int64()

@@ -263,6 +263,39 @@ def test_preemptible_pair_work_on_finer_items():
     assert np.abs(F1 - F0).max() <= 1e-9 * np.sqrt(np.mean(F0 ** 2))
 
 
+def test_medium_and_small_requests_overtake_a_large_batch():
+    """Three classes: express (small, highest priority), medium lanes (middle
+    priority, preemptible) and bulk (lowest, preemptible).  A medium request
+    submitted while a large one runs finishes long before it; a small one
+    submitted while both run finishes before the medium one; all three agree
+    with direct calls."""
+    import time
+    w = I.SERVING_PERIODIC
+    big = I.uniform_pm1(200000, w.box, seed_offset=152)
+    medium = I.uniform_pm1(40000, w.box, seed_offset=153)
+    small = I.uniform_pm1(2000, w.box, seed_offset=154)
+    with hs().Server(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32", lanes=3, max_batch=4,
+                     express_lanes=1, express_max_n=20000, mid_lanes=1, mid_max_n=60000) as srv:
+        tb = srv.submit(*big)
+        time.sleep(0.03)  # the large request is on the GPU
+        tm = srv.submit(*medium)
+        time.sleep(0.002)
+        ts = srv.submit(*small)
+        code_s, E_s, F_s, info_s = srv.result(ts)
+        code_m, E_m, F_m, info_m = srv.result(tm)
+        code_b, E_b, F_b, info_b = srv.result(tb)
+    assert code_s == 0 and code_m == 0 and code_b == 0
+    print(f"\nlarge {info_b['latency_ms']:.1f} ms, medium {info_m['latency_ms']:.1f} ms, "
+          f"small {info_s['latency_ms']:.1f} ms")
+    assert info_m["latency_ms"] < 0.5 * (info_b["latency_ms"] - 30.0), (info_m, info_b)
+    assert info_s["latency_ms"] < info_m["latency_ms"], (info_s, info_m)
+    with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan:
+        for (sx, sq), E, F in ((small, E_s, F_s), (medium, E_m, F_m), (big, E_b, F_b)):
+            U1, F1, _, _ = plan.energy_forces(sx, sq)
+            assert rel_energy_err(E, U1, sq) <= TOL["fp32"]["energy"]
+            assert rms(F - F1) <= TOL["fp32"]["force_rms"] * rms(F1)
+
+
 def test_small_request_overtakes_a_large_batch():
     """Express lane (high-priority stream) and bulk lane (preemptible pair
     work): a small request submitted while a large one runs finishes long

@@ -294,6 +294,25 @@ int launch_monitor_sphere(int K, double R0, const double L[3], double4_32a *out6
 int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *out64, float4 *hi, float4 *lo,
                          cudaStream_t st);
 int launch_quadrature(int F2, int F1, double Rs, double4_32a *dirs, cudaStream_t st);
+// Coefficients of the fully normalised recurrence of the orthonormal real
+// solid harmonics, Pbar_n^m = norm(n, m) Pi_n^m (every order up to
+// kBasisTableMaxP, independent of a plan's P), each as an FP32 pair hi + lo:
+//   Pbar_m^m = D_m,  Pbar_{m+1}^m = E_m z,
+//   Pbar_n^m = a_nm z Pbar_{n-1}^m - b_nm r2 Pbar_{n-2}^m  (n >= m + 2),
+//   a_nm = sqrt((4n^2 - 1)/(n^2 - m^2)),
+//   b_nm = sqrt((2n+1)((n-1)^2 - m^2)/((2n-3)(n^2 - m^2))),
+//   D_0 = 1/sqrt(4 pi), D_m = D_{m-1} sqrt((2m+1)/(2m)) (times sqrt 2 at m = 1),
+//   E_m = sqrt(2m+3) D_m.
+// Passed to kernels by value (27.5 KB of parameters).
+constexpr int kBasisTableMaxP = 40;
+struct BasisDfTables {
+    float2 a[kBasisTableMaxP + 1][kBasisTableMaxP + 1];  // a_nm at [m][n] (n >= m + 2)
+    float2 b[kBasisTableMaxP + 1][kBasisTableMaxP + 1];  // b_nm at [m][n]
+    float2 d[kBasisTableMaxP + 1];                       // D_m
+    float2 e[kBasisTableMaxP + 1];                       // E_m
+};
+const BasisDfTables &basis_df_tables();  // computed once on the host, in FP64
+
 // orthonormalisation constant of the real solid harmonic (n, m), m >= 0:
 // sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!)
 double basis_norm(int n, int m);

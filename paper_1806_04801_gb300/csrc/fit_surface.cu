@@ -552,28 +552,35 @@ __global__ void series_field_kernel(const SysDesc *sys, int nsys, int P, double 
 
 }  // namespace
 
-// FP32 form of series_field_kernel for the reduced precisions: the same
-// recurrences in FP32 (positions from the split words, coefficients
-// pre-multiplied by the normalisation and the reciprocals 1/(n - m) staged in
-// shared memory), the sums over n folded into double-float accumulators after
-// every m.  FP64 issue is slow on this part; this evaluates the fitted
-// series at O(N N_b) FP32 cost.  Pi_m^m = (2m - 1)!! leaves the FP32 range
-// near m = 29 (57!! ~ 6.5e38) and the normalisation nears FP32's smallest
-// normal number there, so orders above the paper's largest (P = 25) take the
-// FP64 kernel.
-constexpr int kSeriesMaxP = 25;
-__global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, double inv_rs, const double *norm,
-                                         const double *A, const float4 *src_hi, const float4 *src_lo,
-                                         double *phi_out, double *e_out)
+// FP32 form of series_field_kernel for the reduced precisions: the fully
+// normalised recurrence (the coefficients of basis_df_tables, high words;
+// every intermediate stays of order (r/Rs)^n, so no order leaves the FP32
+// range) and its derivatives in z and r2,
+//   d/dz  Pbar_n = a (Pbar_{n-1} + z d/dz Pbar_{n-1}) - b r2 d/dz Pbar_{n-2},
+//   d/dr2 Pbar_n = a z d/dr2 Pbar_{n-1} - b (Pbar_{n-2} + r2 d/dr2 Pbar_{n-2}),
+// in FP32 (positions from the split words, coefficients staged in shared
+// memory), the sums over n folded into double-float accumulators after every
+// m.  FP64 issue is slow on this part; this evaluates the fitted series at
+// O(N N_b) FP32 cost.
+__global__ void series_field_fp32_kernel(const __grid_constant__ BasisDfTables tabs, const SysDesc *sys, int nsys,
+                                         int P, double inv_rs, const double *A, const float4 *src_hi,
+                                         const float4 *src_lo, double *phi_out, double *e_out)
 {
-    extern __shared__ float ssm[];  // [Nb] coefficients A_k norm_k, then [P + 1] reciprocals
+    extern __shared__ float ssm[];  // [Nb] coefficients A_k, a[m][n], b[m][n] ((P+1)^2 each), D, E
     const int s = blockIdx.y;
     const SysDesc sd = sys[s];
-    const int Nb = (P + 1) * (P + 1);
-    float *an = ssm, *rinv = ssm + Nb;
+    const int W = P + 1, Nb = W * W;
+    float *an = ssm, *ta = ssm + Nb, *tb = ta + W * W, *td = tb + W * W, *te = td + W;
     const double *a = A + (long long)s * Nb;
-    for (int k = threadIdx.x; k < Nb; k += blockDim.x) an[k] = (float)(a[k] * norm[k]);
-    for (int k = threadIdx.x; k <= P; k += blockDim.x) rinv[k] = k > 0 ? 1.0f / (float)k : 0.f;
+    for (int k = threadIdx.x; k < Nb; k += blockDim.x) {
+        an[k] = (float)a[k];
+        ta[k] = tabs.a[k / W][k % W].x;
+        tb[k] = tabs.b[k / W][k % W].x;
+    }
+    for (int k = threadIdx.x; k <= P; k += blockDim.x) {
+        td[k] = tabs.d[k].x;
+        te[k] = tabs.e[k].x;
+    }
     __syncthreads();
     const long long i = sd.sp_lo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sd.sp_lo + sd.sp_n) return;
@@ -583,7 +590,6 @@ __global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, do
     const float r2 = fmaf(x, x, fmaf(y, y, z * z));
     float2 phi = make_float2(0.f, 0.f), gx = phi, gy = phi, gz = phi;
     float cm = 1.f, sm = 0.f, cp = 0.f, sp = 0.f;  // (x+iy)^m and (x+iy)^(m-1)
-    float pmm = 1.f, two_m_1 = -1.f;
     for (int m = 0; m <= P; ++m) {
         if (m > 0) {
             cp = cm;
@@ -591,29 +597,26 @@ __global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, do
             const float c2 = cm * x - sm * y;
             sm = sm * x + cm * y;
             cm = c2;
-            pmm *= two_m_1;
         }
         const float fm = (float)m;
         float p1 = 0.f, p2 = 0.f, z1 = 0.f, z2 = 0.f, q1 = 0.f, q2 = 0.f;
-        float a_n = two_m_1 + 4.f, b_n = 2.f * fm + 1.f;  // 2n - 1 and n + m - 1 at n = m + 2
         float fp = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+        const float *am = ta + m * W, *bm = tb + m * W;
         for (int n = m; n <= P; ++n) {
             float pn, dz, dq;
             if (n == m) {
-                pn = pmm;
+                pn = td[m];
                 dz = 0.f;
                 dq = 0.f;
             } else if (n == m + 1) {
-                pn = (two_m_1 + 2.f) * z * pmm;
-                dz = (two_m_1 + 2.f) * pmm;
+                pn = te[m] * z;
+                dz = te[m];
                 dq = 0.f;
             } else {
-                const float inv = rinv[n - m];
-                pn = (a_n * z * p1 - b_n * r2 * p2) * inv;
-                dz = (a_n * (p1 + z * z1) - b_n * r2 * z2) * inv;
-                dq = (a_n * z * q1 - b_n * (p2 + r2 * q2)) * inv;
-                a_n += 2.f;
-                b_n += 1.f;
+                const float ca = am[n], cb = bm[n];
+                pn = ca * z * p1 - cb * r2 * p2;
+                dz = ca * (p1 + z * z1) - cb * r2 * z2;
+                dq = ca * z * q1 - cb * (p2 + r2 * q2);
             }
             p2 = p1; p1 = pn;
             z2 = z1; z1 = dz;
@@ -636,7 +639,6 @@ __global__ void series_field_fp32_kernel(const SysDesc *sys, int nsys, int P, do
         gx = df_add(gx, fx);
         gy = df_add(gy, fy);
         gz = df_add(gz, fz);
-        two_m_1 += 2.f;
     }
     const long long o = sd.part_off + i;
     phi_out[o] = (double)phi.x + (double)phi.y;
@@ -650,10 +652,10 @@ int launch_series_field(const SysDesc *sys, int nsys, long long max_n, int P, do
                         double *phi_out, double *e_out, cudaStream_t st)
 {
     dim3 grid((unsigned)((max_n + 127) / 128), nsys);
-    if (!src64 && src_hi && P <= kSeriesMaxP) {
-        const size_t smem = sizeof(float) * ((size_t)(P + 1) * (P + 1) + (size_t)(P + 1));
-        series_field_fp32_kernel<<<grid, 128, smem, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, phi_out,
-                                                          e_out);
+    if (!src64 && src_hi && P <= kBasisTableMaxP) {
+        const size_t smem = sizeof(float) * (3 * (size_t)(P + 1) * (P + 1) + 2 * (size_t)(P + 1));
+        series_field_fp32_kernel<<<grid, 128, smem, st>>>(basis_df_tables(), sys, nsys, P, 1.0 / Rs, A, src_hi, src_lo,
+                                                          phi_out, e_out);
     } else {
         series_field_kernel<<<grid, 128, 0, st>>>(sys, nsys, P, 1.0 / Rs, norm, A, src_hi, src_lo, src64, phi_out,
                                                   e_out);

@@ -329,38 +329,6 @@ __device__ __forceinline__ double df_to_f64_scaled(float2 v, uint32_t kb, int k)
 // kernel parameter; each block copies the (P+1)^2 it needs to shared memory.
 constexpr int kBasisDfWarps = 2;  // warps per block
 
-struct BasisDfTables {
-    float2 a[kBasisMaxP + 1][kBasisMaxP + 1];  // a_nm at [m][n] (n >= m + 2)
-    float2 b[kBasisMaxP + 1][kBasisMaxP + 1];  // b_nm at [m][n]
-    float2 d[kBasisMaxP + 1];                  // D_m
-    float2 e[kBasisMaxP + 1];                  // sqrt(2m + 3) D_m
-};
-
-const BasisDfTables &basis_df_tables()
-{
-    static const BasisDfTables t = [] {
-        BasisDfTables v{};
-        auto pair = [](double x) {
-            const float h = (float)x;
-            return make_float2(h, (float)(x - (double)h));
-        };
-        for (int m = 0; m <= kBasisMaxP; ++m) {
-            for (int n = m + 2; n <= kBasisMaxP; ++n) {
-                const double dn = n, dm = m, q = dn * dn - dm * dm;
-                v.a[m][n] = pair(std::sqrt((4.0 * dn * dn - 1.0) / q));
-                v.b[m][n] = pair(std::sqrt((2.0 * dn + 1.0) * ((dn - 1.0) * (dn - 1.0) - dm * dm) / ((2.0 * dn - 3.0) * q)));
-            }
-            double d = 1.0 / std::sqrt(4.0 * kPi);
-            for (int j = 1; j <= m; ++j) d *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
-            if (m > 0) d *= std::sqrt(2.0);
-            v.d[m] = pair(d);
-            v.e[m] = pair(std::sqrt(2.0 * m + 3.0) * d);
-        }
-        return v;
-    }();
-    return t;
-}
-
 __host__ __device__ constexpr size_t basis_df_smem_bytes(int P, int warps)
 {
     // tables a, b ((P+1)^2 each), D, E (P+1 each); per warp: 4 (P+1) state
@@ -669,6 +637,31 @@ int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *o64, 
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;
+}
+
+const BasisDfTables &basis_df_tables()
+{
+    static const BasisDfTables t = [] {
+        BasisDfTables v{};
+        auto pair = [](double x) {
+            const float h = (float)x;
+            return make_float2(h, (float)(x - (double)h));
+        };
+        for (int m = 0; m <= kBasisTableMaxP; ++m) {
+            for (int n = m + 2; n <= kBasisTableMaxP; ++n) {
+                const double dn = n, dm = m, q = dn * dn - dm * dm;
+                v.a[m][n] = pair(std::sqrt((4.0 * dn * dn - 1.0) / q));
+                v.b[m][n] = pair(std::sqrt((2.0 * dn + 1.0) * ((dn - 1.0) * (dn - 1.0) - dm * dm) / ((2.0 * dn - 3.0) * q)));
+            }
+            double d = 1.0 / std::sqrt(4.0 * kPi);
+            for (int j = 1; j <= m; ++j) d *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
+            if (m > 0) d *= std::sqrt(2.0);
+            v.d[m] = pair(d);
+            v.e[m] = pair(std::sqrt(2.0 * m + 3.0) * d);
+        }
+        return v;
+    }();
+    return t;
 }
 
 double basis_norm(int n, int m)

@@ -735,12 +735,13 @@ def test_series_far_field(bc):
     assert abs(Ui - U) <= 1e-7 * abs(U)
 
 
-@pytest.mark.parametrize("P", [25, 30])
+@pytest.mark.parametrize("P", [25, 30, 40])
 def test_series_far_field_high_order(P):
-    """The series far field at high harmonic order: the FP32 kernel serves
-    orders up to the paper's largest (P = 25), the FP64 kernel above it
-    (where (2m - 1)!! leaves the FP32 range); both agree with the FP64 path's
-    series and with the surface images of the same plan."""
+    """The series far field at high harmonic order: the FP32 kernel runs the
+    fully normalised recurrence, whose values stay of order (r/Rs)^n, so it
+    serves every order up to the largest (the unnormalised (2m - 1)!! would
+    leave the FP32 range near m = 29); it agrees with the FP64 path's series
+    and, up to P = 30, with the surface images of the same plan."""
     w = I.Workload(f"series-p{P}", (1.0, 1.0, 1.0), I.PERIODIC, P, 2.0 * 0.5 * 3.0 ** 0.5, 6000, 2 * (P + 1) ** 2)
     xyz, q = I.random_neutral(256, w.box, seed_offset=60 + P)
     dx, dq = to_dev(xyz, q)
@@ -758,6 +759,8 @@ def test_series_far_field_high_order(P):
     assert rms(Fs - F64) <= 1e-5 * rms(F64)
     # the surface images add the quadrature's error for harmonics up to
     # degree P (N_o = 5928 directions): a looser, method-level bound
+    if P > 30:
+        return
     Ui, Fi = out[("fp32", "images")]
     assert rel_energy_err(Ui, U64, q) <= 1e-5, (Ui, U64)
     assert rms(Fi - F64) <= 1e-4 * rms(F64)

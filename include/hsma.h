@@ -319,7 +319,7 @@ int hsma_plan_set_tuning(hsma_plan_t plan, const hsma_tuning *t);
 int hsma_plan_get_tuning(hsma_plan_t plan, int nsys, const int64_t *offsets, hsma_tuning *out);
 
 /* Autotuner: runs the update step on this batch for each candidate
- * (pair_variant 14, 17, 12, 13, 2 x items_per_slot 8, 16, 24, 48, 96; FP64:
+ * (pair_variant 14, 17, 12, 13, 2 x items_per_slot 8, 16, 24, 48; FP64:
  * items only), keeps the fastest as
  * the plan's entry for this work size, returns it in *best, and appends it as
  * one JSON line to cache_path (if not NULL).  Device inputs are recommended

@@ -1730,7 +1730,7 @@ int hsma_autotune(hsma_plan_t pl, int nsys, const int64_t *offsets, const hsma_p
     // candidates: the packed variants and the two-target scalar loop for
     // reference (4, 5, 15, 16 never won on this part; they stay selectable)
     const int variants[5] = {14, 17, 12, 13, 2};
-    const int items[5] = {8, 16, 24, 48, 96};
+    const int items[4] = {8, 16, 24, 48};
     for (int v = 0; v < (pl->precision == HSMA_FP64 ? 1 : 5); ++v)
         for (int i : items) cands.push_back(hsma_tuning{variants[v], i, 0.0});
     hsma_tuning win{14, 48, 1e300};

@@ -188,7 +188,7 @@ def test_autotuner_and_both_kernel_variants(tmp_path):
         plan.set_tuning(None, None)
         cache = str(tmp_path / "tune.jsonl")
         best = plan.autotune(dx, dq, off, cache_path=cache)
-        assert best["pair_variant"] in (14, 17, 12, 13, 2) and best["items_per_slot"] in (8, 16, 24, 48, 96) and best["ms"] > 0
+        assert best["pair_variant"] in (14, 17, 12, 13, 2) and best["items_per_slot"] in (8, 16, 24, 48) and best["ms"] > 0
         assert plan.get_tuning(off)["pair_variant"] == best["pair_variant"]
     with hs().Plan(w.box, w.bc, w.p, w.R, w.Q, w.Kmon, precision="fp32") as plan2:
         assert (plan2.get_tuning(off)["pair_variant"], plan2.get_tuning(off)["items_per_slot"]) == (17, 48)  # defaults

@@ -40,7 +40,8 @@ RECIPE_MAX_SM_MHZ = 2070.0
 # periodic N=100000 workload, from the ncu capture summarised in
 # profiles/pair_fp32_kernel_periodic_N100000_dram.md (current kernel build),
 # keyed by (N, pair variant, items per slot) of the captured launch.
-PAIR_FP32_TRAFFIC_BYTES = {(100_000, 17, 48): 361.16e6, (100_000, 14, 48): 356.89e6}
+PAIR_FP32_TRAFFIC_BYTES = {(100_000, 17, 48): 361.16e6, (100_000, 14, 48): 356.89e6,
+                           (100_000, 17, 96): 726.99e6, (100_000, 14, 96): 710.68e6}
 OPS_SURFACE = 45                 # FP32 lane instructions per particle-direction pair of the surface kernel
 
 

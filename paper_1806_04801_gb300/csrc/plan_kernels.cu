@@ -100,103 +100,137 @@ __global__ void quadrature_kernel(int F2, int F1, double Rs, double4_32a *dirs)
     dirs[2 * j + 1] = make_double4_32a(-st * cos(ph), -st * sin(ph), ct, w);
 }
 
-// Orthonormal real solid harmonics (|x|/Rs)^n Y_nm by the Cartesian
-// recurrence: with (x, y, z) scaled by 1/Rs and r2 = x^2 + y^2 + z^2,
-//   (x + i y)^m = C_m + i S_m,
-//   Pi_m^m = (2m-1)!!,  Pi_{m+1}^m = (2m+1) z Pi_m^m,
-//   (n-m) Pi_n^m = (2n-1) z Pi_{n-1}^m - (n+m-1) r2 Pi_{n-2}^m,
-// so that r^n P_n^m(cos theta) e^{i m phi} = Pi_n^m (x + i y)^m.  Column
-// k = n^2 + n + m holds norm[k] * Pi_n^|m| * (C_m for m >= 0, S_|m| for m < 0),
-// norm[k] = sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-|m|)!/(n+|m|)!).
-// One thread per point; the recurrence runs over m outer, n inner.  The
-// divisions by (n - m) use a table of reciprocals and the integer factors
-// run as FP64 counters (FP64 issue is slow on this part and a division costs
-// many FP64 instructions); the reciprocals and the normalisation constants
-// sit in shared memory.  Each thread writes its own row of N_b values, so a
-// row's 32-byte sectors fill over many stores: the grid is persistent and
-// sized so that the rows in flight stay well inside L2 (with one thread per
-// point over the whole grid, partially written sectors were evicted and read
-// back: 3.5 GB of DRAM reads for 1.35 GB written; 4e6 points at p = 12 took
-// 15.5 ms, against 8.0 ms with 24 MB of rows in flight, one block per SM).
+// Orthonormal real solid harmonics (|x|/Rs)^n Y_nm by the fully normalised
+// Cartesian recurrence: with (x, y, z) scaled by 1/Rs, r2 = x^2 + y^2 + z^2,
+// (x + i y)^m = C_m + i S_m and Pbar_n^m = norm(n, m) Pi_n^m, where
+// r^n P_n^m(cos theta) e^{i m phi} = Pi_n^m (x + i y)^m and
+// norm(n, m) = sqrt((2 - delta_m0)(2n+1)/(4 pi) (n-m)!/(n+m)!),
+//   Pbar_m^m = D_m,  Pbar_{m+1}^m = E_m z,
+//   Pbar_n^m = a_nm z Pbar_{n-1}^m - b_nm r2 Pbar_{n-2}^m  (n >= m + 2)
+// with the coefficients of basis_f64_tables (the plain recurrence
+// (n-m) Pi_n^m = (2n-1) z Pi_{n-1}^m - (n+m-1) r2 Pi_{n-2}^m rescaled by the
+// norms, so neither (2m-1)!! nor the norm products appear).  Column
+// k = n^2 + n + m holds Pbar_n^|m| (C_m for m >= 0, S_|m| for m < 0).
+// Layout of the work as in basis_df_kernel below: a warp takes 32
+// consecutive points and runs the degree outer, m inner, with the recurrence
+// state in shared memory and each degree's row segments stored coalesced from
+// a staging tile, so the output's sectors are written once (the m-outer order
+// of one thread per row kept every row's sectors partly written until the
+// row was done: L2 evicted and re-read them, and capping the rows in flight
+// left one block per SM).  Four FP64 operations per recurrence step and one
+// per stored value; FP64 issue is slow on this part.
 constexpr int kBasisMaxP = 40;
-constexpr int kBasisThreads = 128;
-constexpr double kBasisRowsInFlightBytes = 24.0 * 1024 * 1024;
+constexpr int kBasisWarps = 2;  // warps per block
+static_assert(kBasisMaxP == kBasisTableMaxP, "one coefficient table serves both basis forms");
 
-// The normalisation constants of every n, m <= kBasisMaxP at k = n^2 + n + m,
-// computed once on the host and passed by value (no device buffer).
-struct BasisNormTable {
-    double v[(kBasisMaxP + 1) * (kBasisMaxP + 1)];
+// The recurrence coefficients of every n, m <= kBasisMaxP in FP64, computed
+// once on the host and passed to the kernel by value (no device buffer).
+struct BasisF64Tables {
+    double a[kBasisMaxP + 1][kBasisMaxP + 1];  // a_nm at [m][n] (n >= m + 2)
+    double b[kBasisMaxP + 1][kBasisMaxP + 1];  // b_nm at [m][n]
+    double d[kBasisMaxP + 1];                  // D_m
+    double e[kBasisMaxP + 1];                  // E_m = sqrt(2m + 3) D_m
 };
 
-const BasisNormTable &basis_norm_table()
+const BasisF64Tables &basis_f64_tables()
 {
-    static const BasisNormTable t = [] {
-        BasisNormTable v{};
-        for (int n = 0; n <= kBasisMaxP; ++n)
-            for (int m = -n; m <= n; ++m) v.v[n * n + n + m] = basis_norm(n, m < 0 ? -m : m);
+    static const BasisF64Tables t = [] {
+        BasisF64Tables v{};
+        for (int m = 0; m <= kBasisMaxP; ++m) {
+            for (int n = m + 2; n <= kBasisMaxP; ++n) {
+                const double dn = n, dm = m, q = dn * dn - dm * dm;
+                v.a[m][n] = std::sqrt((4.0 * dn * dn - 1.0) / q);
+                v.b[m][n] = std::sqrt((2.0 * dn + 1.0) * ((dn - 1.0) * (dn - 1.0) - dm * dm) / ((2.0 * dn - 3.0) * q));
+            }
+            double d = 1.0 / std::sqrt(4.0 * kPi);
+            for (int j = 1; j <= m; ++j) d *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
+            if (m > 0) d *= std::sqrt(2.0);
+            v.d[m] = d;
+            v.e[m] = std::sqrt(2.0 * m + 3.0) * d;
+        }
         return v;
     }();
     return t;
 }
 
-__global__ void __launch_bounds__(kBasisThreads) basis_kernel(const __grid_constant__ BasisNormTable norm_t, int P,
-                                                              double inv_rs, long long np,
-                                                              const double *__restrict__ pts, int stride,
-                                                              double *__restrict__ out, long long ld)
+__host__ __device__ constexpr size_t basis_smem_bytes(int P, int warps)
 {
-    extern __shared__ double bsm[];  // [P + 1] reciprocals, then [(P + 1)^2] normalisation
-    double *rinv = bsm, *norm = bsm + (P + 1);
-    const int Nb = (P + 1) * (P + 1);
-    for (int k = threadIdx.x; k <= P; k += blockDim.x) rinv[k] = k > 0 ? 1.0 / (double)k : 0.0;
-    for (int k = threadIdx.x; k < Nb; k += blockDim.x) norm[k] = norm_t.v[k];
+    // tables a, b ((P+1)^2 each), D, E (P+1 each); per warp: 4 (P+1) state
+    // slots x 32 lanes and a 32 x (2P+1) staging tile (8-byte words)
+    return 8 * ((size_t)2 * (P + 1) * (P + 1) + (size_t)2 * (P + 1) +
+                (size_t)warps * 32 * ((size_t)4 * (P + 1) + (size_t)(2 * P + 1)));
+}
+
+__global__ void __launch_bounds__(32 * kBasisWarps) basis_kernel(const __grid_constant__ BasisF64Tables tabs, int P,
+                                                                 double inv_rs, long long np,
+                                                                 const double *__restrict__ pts, int stride,
+                                                                 double *__restrict__ out, int ld)
+{
+    extern __shared__ double bsm[];
+    const int W = P + 1, pitch = 2 * P + 1;
+    double *ta = bsm, *tb = bsm + W * W, *td = tb + W * W, *te = td + W;
+    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
+        ta[t] = tabs.a[t / W][t % W];
+        tb[t] = tabs.b[t / W][t % W];
+    }
+    for (int m = threadIdx.x; m <= P; m += blockDim.x) {
+        td[m] = tabs.d[m];
+        te[m] = tabs.e[m];
+    }
     __syncthreads();
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np;
-         i += (long long)gridDim.x * blockDim.x) {
-        double x = pts[i * stride] * inv_rs, y = pts[i * stride + 1] * inv_rs, z = pts[i * stride + 2] * inv_rs;
-        double r2 = x * x + y * y + z * z;
-        double *o = out + i * ld;
-        double cm = 1.0, sm = 0.0;   // (x + i y)^m
-        double pmm = 1.0;            // Pi_m^m
-        double two_m_1 = -1.0;       // 2m - 1
-        for (int m = 0; m <= P; ++m) {
-            if (m > 0) {
-                double c2 = cm * x - sm * y;
-                sm = sm * x + cm * y;
-                cm = c2;
-                pmm *= two_m_1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *wb = te + W + (size_t)warp * 32 * (4 * W + pitch);
+    double *pst = wb + lane;  // Pbar at even, then odd degrees; slot m at [32 m]
+    double *cs = wb + 64 * W + lane, *ss = wb + 96 * W + lane;
+    double *stage = wb + 128 * W;  // [32 rows][pitch]
+    const long long ngroups = (np + 31) / 32;
+    for (long long g = (long long)blockIdx.x * (blockDim.x >> 5) + warp; g < ngroups;
+         g += (long long)gridDim.x * (blockDim.x >> 5)) {
+        const long long i0 = g * 32;
+        const int rows = (int)min(32LL, np - i0);
+        const long long i = i0 + min(lane, rows - 1);  // lanes past the end repeat the last point, unwritten
+        const double x = pts[i * stride] * inv_rs, y = pts[i * stride + 1] * inv_rs, z = pts[i * stride + 2] * inv_rs;
+        const double r2 = x * x + y * y + z * z;
+        double C = 1.0, S = 0.0;  // (x + i y)^n
+        double *sc0 = stage + lane * pitch;
+        double *og = out + i0 * ld;
+        for (int n = 0; n <= P; ++n) {
+            double *cur = pst + (n & 1) * 32 * W, *prv = pst + ((n & 1) ^ 1) * 32 * W;
+            double *sc = sc0 + n;  // column n + m holds the cosine part, n - m the sine part
+            if (n > 0) {
+                const double c2 = C * x - S * y;
+                S = S * x + C * y;
+                C = c2;
             }
-            // n = m and n = m + 1
-            double p2 = pmm, p1 = (two_m_1 + 2.0) * z * pmm;  // Pi_m^m, Pi_{m+1}^m
-            {
-                const int kc = m * m + m + m;
-                const double np0 = norm[kc] * pmm;
-                o[kc] = np0 * cm;
-                if (m > 0) o[m * m] = norm[m * m] * pmm * sm;  // n = m, index n^2 + n - m
+            cs[32 * n] = C;
+            ss[32 * n] = S;
+            cur[32 * n] = td[n];  // m = n
+            sc[n] = td[n] * C;
+            if (n > 0) {
+                sc[-n] = td[n] * S;
+                const int m = n - 1;  // m = n - 1
+                const double p = te[m] * z;
+                cur[32 * m] = p;
+                sc[m] = p * cs[32 * m];
+                if (m > 0) sc[-m] = p * ss[32 * m];
             }
-            if (m + 1 <= P) {
-                const int n = m + 1, kc = n * n + n + m;
-                o[kc] = norm[kc] * p1 * cm;
-                if (m > 0) {
-                    const int ks = n * n + n - m;
-                    o[ks] = norm[ks] * p1 * sm;
-                }
+            const double *an = ta + n, *bn = tb + n;
+            for (int m = 0; m + 2 <= n; ++m) {
+                const double pn = fma(an[m * W] * z, prv[32 * m], -(bn[m * W] * r2) * cur[32 * m]);
+                cur[32 * m] = pn;
+                sc[m] = pn * cs[32 * m];
+                if (m > 0) sc[-m] = pn * ss[32 * m];
             }
-            double a = two_m_1 + 4.0;        // 2n - 1 at n = m + 2
-            double b = 2.0 * m + 1.0;        // n + m - 1 at n = m + 2
-            for (int n = m + 2; n <= P; ++n) {
-                const double pn = (a * z * p1 - b * r2 * p2) * rinv[n - m];
-                p2 = p1;
-                p1 = pn;
-                a += 2.0;
-                b += 1.0;
-                const int kc = n * n + n + m;
-                o[kc] = norm[kc] * pn * cm;
-                if (m > 0) {
-                    const int ks = n * n + n - m;
-                    o[ks] = norm[ks] * pn * sm;
-                }
+            __syncwarp();
+            const int wd = 2 * n + 1, tot = rows * wd;
+            const uint32_t cw = ((1u << 20) + (uint32_t)wd - 1u) / (uint32_t)wd;  // ceil(2^20 / (2n + 1))
+            double *ob = og + n * n;
+#pragma unroll 4
+            for (int f = lane; f < tot; f += 32) {
+                const int r = (int)(((uint32_t)f * cw) >> 20), j = f - r * wd;
+                ob[r * ld + j] = stage[r * pitch + j];
             }
-            two_m_1 += 2.0;
+            __syncwarp();
         }
     }
 }
@@ -642,22 +676,19 @@ int launch_monitor_faces(const int cnt[6], const double L[3], double4_32a *o64, 
 const BasisDfTables &basis_df_tables()
 {
     static const BasisDfTables t = [] {
+        const BasisF64Tables &f = basis_f64_tables();
         BasisDfTables v{};
         auto pair = [](double x) {
             const float h = (float)x;
             return make_float2(h, (float)(x - (double)h));
         };
         for (int m = 0; m <= kBasisTableMaxP; ++m) {
-            for (int n = m + 2; n <= kBasisTableMaxP; ++n) {
-                const double dn = n, dm = m, q = dn * dn - dm * dm;
-                v.a[m][n] = pair(std::sqrt((4.0 * dn * dn - 1.0) / q));
-                v.b[m][n] = pair(std::sqrt((2.0 * dn + 1.0) * ((dn - 1.0) * (dn - 1.0) - dm * dm) / ((2.0 * dn - 3.0) * q)));
+            for (int n = 0; n <= kBasisTableMaxP; ++n) {
+                v.a[m][n] = pair(f.a[m][n]);
+                v.b[m][n] = pair(f.b[m][n]);
             }
-            double d = 1.0 / std::sqrt(4.0 * kPi);
-            for (int j = 1; j <= m; ++j) d *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
-            if (m > 0) d *= std::sqrt(2.0);
-            v.d[m] = pair(d);
-            v.e[m] = pair(std::sqrt(2.0 * m + 3.0) * d);
+            v.d[m] = pair(f.d[m]);
+            v.e[m] = pair(f.e[m]);
         }
         return v;
     }();
@@ -684,17 +715,19 @@ int launch_basis(int P, double Rs, long long np, const double *pts, int stride, 
                  cudaStream_t st)
 {
     if (np <= 0) return HSMA_OK;
-    if (P < 0 || P > kBasisMaxP) return HSMA_E_ARG;
-    int dev = 0, sms = 1;
+    // the kernel indexes a group's 32 rows with 32-bit offsets r ld + column
+    if (P < 0 || P > kBasisMaxP || ld < (long long)(P + 1) * (P + 1) || ld > (1LL << 26)) return HSMA_E_ARG;
+    int dev = 0, sms = 1, per_sm = 0;
     HSMA_CUDA_TRY(cudaGetDevice(&dev));
     HSMA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const double row_bytes = 8.0 * (double)(P + 1) * (double)(P + 1);
-    const long long in_flight =
-        std::max<long long>(sms, (long long)(kBasisRowsInFlightBytes / row_bytes) / kBasisThreads);
-    const long long blocks = std::min<long long>((np + kBasisThreads - 1) / kBasisThreads, in_flight);
-    const size_t smem = sizeof(double) * ((size_t)(P + 1) + (size_t)(P + 1) * (P + 1));
-    basis_kernel<<<(unsigned)blocks, kBasisThreads, smem, st>>>(basis_norm_table(), P, 1.0 / Rs, np, pts, stride,
-                                                                 out, ld);
+    const size_t smem = basis_smem_bytes(P, kBasisWarps);
+    HSMA_CUDA_TRY(cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HSMA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, basis_kernel, 32 * kBasisWarps, smem));
+    if (per_sm < 1) return HSMA_E_ARG;
+    const long long groups = (np + 31) / 32;
+    const long long blocks = std::min<long long>((groups + kBasisWarps - 1) / kBasisWarps, (long long)sms * per_sm);
+    basis_kernel<<<(unsigned)blocks, 32 * kBasisWarps, smem, st>>>(basis_f64_tables(), P, 1.0 / Rs, np, pts, stride,
+                                                                   out, (int)ld);
     HSMA_LAUNCHED();
     HSMA_CUDA_TRY(cudaGetLastError());
     return HSMA_OK;

@@ -465,8 +465,8 @@ int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const dou
  * precision HSMA_FP64: the recurrence in FP64 (relative error ~1e-16 of the
  * row's scale (|x|/Rs)^n); HSMA_FP32_ACC64: the same recurrence, fully
  * normalised, in double-float arithmetic (pairs of FP32 words) on the FP32
- * pipe, several times faster on this part and accurate to ~1e-14 of that
- * scale.  Each point is scaled by a power of two first, so neither form
+ * pipe, faster on this part (whose FP64 issue rate is low) and accurate to
+ * ~1e-14 of that scale.  Each point is scaled by a power of two first, so neither form
  * underflows for points near the origin.  A point with a non-finite
  * coordinate gets non-finite values (NaN or infinity) wherever they depend
  * on it.  Allocates no device memory.  Returns once out holds the basis.

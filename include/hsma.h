@@ -462,12 +462,12 @@ int hsma_coulomb_sum_static(int64_t ns, const double *src, int64_t nt, const dou
  * np x 3, out np x (p+1)^2 row-major, FP64): the orthonormal real solid
  * harmonics (|x|/Rs)^n Y_nm, index k = n^2 + n + m, m > 0 the cosine and
  * m < 0 the sine part, without the Condon-Shortley phase; 0 <= p <= 40.
- * precision HSMA_FP64: the recurrence in FP64 (relative error ~1e-16 of the
- * row's scale (|x|/Rs)^n); HSMA_FP32_ACC64: the same recurrence, fully
- * normalised, in double-float arithmetic (pairs of FP32 words) on the FP32
+ * precision HSMA_FP64: the fully normalised recurrence in FP64 (relative
+ * error ~1e-16 of the row's scale (|x|/Rs)^n); HSMA_FP32_ACC64: the same
+ * recurrence in double-float arithmetic (pairs of FP32 words) on the FP32
  * pipe, faster on this part (whose FP64 issue rate is low) and accurate to
- * ~1e-14 of that scale.  Each point is scaled by a power of two first, so neither form
- * underflows for points near the origin.  A point with a non-finite
+ * ~1e-14 of that scale; it scales each point by a power of two first, so it
+ * does not underflow for points near the origin.  A point with a non-finite
  * coordinate gets non-finite values (NaN or infinity) wherever they depend
  * on it.  Allocates no device memory.  Returns once out holds the basis.
  * Errors: HSMA_E_ARG (p, Rs, np, null pointers, precision), HSMA_E_CUDA. */

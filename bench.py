@@ -114,11 +114,12 @@ def run_basis(steps: int, warmup: int, n: int = 4_000_000, p: int = 12, Rs: floa
     nb = (p + 1) * (p + 1)
     written = n * nb * 8.0
     hbm, how = measured_hbm_gbs()
-    # FP64 operations of the FP64 recurrence per point: per (n, m) with
-    # n >= m + 2 five (two products, a fused difference, the reciprocal), per
-    # stored value two (norm x Pi x C_m or S_m), plus the (x + i y)^m update
+    # FP64 operations of the FP64 form per point (fully normalised
+    # recurrence): per (n, m) with n >= m + 2 four (a_nm z, b_nm r2, a product
+    # and a fused multiply-add), one per stored value (Pbar C_m or S_m), one
+    # per order for E_m z, six per power of (x + i y), three for r2
     pairs = sum(max(0, p - m - 1) for m in range(p + 1))
-    fp64_ops = 5 * pairs + 2 * nb + 4 * p + 8
+    fp64_ops = 4 * pairs + nb + (p + 1) + 6 * p + 3
     gbs = written / (ms / 1000.0) / 1e9
     return {"workload": f"basis-N{n}-p{p} (points uniform in a cube inside the Rs = {Rs} ball)",
             "points": n, "p": p, "N_b": nb, "ms": ms, "points_per_s": n / (ms / 1000.0),
